@@ -1,0 +1,365 @@
+"""Benchmark of the explicit SPFM step on GB300.
+
+Workload (default): spherical grain of radius 150 at the centre of a 512^3
+FP32 grid, lambda = 3, 27-point stencil, TI potential with u || [120]
+(TI_<120>), dF = 0.02, dt = 0.05, periodic boundaries.  A "step" is one
+explicit time step of the whole grid (one launch of the stencil kernel); the
+FP64 interface diagnostics run every 50 steps inside the timed region.
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own replica
+of the workload on its GPU (the path has no exchange step: replicas only) and
+`value` sums the cells all ranks updated over the max-over-ranks time.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead (a
+z-slab of the same grid per step) and prints the same line with
+"impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("SPFM cell-updates/s and % HBM roofline (1 GB300); batched/served vs plain at "
+          "1e-4 vel err; p99")
+UNIT = "cell-updates/s"
+STATS_EVERY = 50
+BYTES_PER_UPDATE = {"f32": 8, "f64": 16, "bf16": 4}   # one read + one write of phi per step
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64", "bf16"])
+    ap.add_argument("--scheme", default="ti120", choices=["ti120", "fd"])
+    ap.add_argument("--n", type=int, default=512, help="grid edge")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_1910_05180_gb300 import workloads as WL
+    w = dict(WL.sphere_512cubed())
+    if args.n != 512:
+        w["nx"] = w["ny"] = w["nz"] = args.n
+        w["ctr"] = ((args.n - 1) / 2.0,) * 3
+        w["R"] = 150.0 * args.n / 512.0
+        w["name"] = f"sphere_{args.n}cubed_R{w['R']:g}"
+    return w
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for ln in f:
+                parts = [x.strip() for x in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1910_05180_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, only while the
+    kernel sources are unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = d.get(kernel_key)
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+# ------------------------------------------------------------------ oracle arm
+
+
+def _oracle_slab(w, nz_slab):
+    import oracle as O
+    p = O.Params(w["nx"], w["ny"], nz_slab, bc=(O.PERIODIC,) * 4 + (O.NOFLUX, O.NOFLUX),
+                 n=w["u"], lam=w["lam"], dx=w["dx"], M=w["M"], Gamma=w["Gamma"], dt=w["dt"],
+                 dF=w["dF"], stencil=w["stencil"], scheme=O.TI_GLOBAL)
+    # the slab is the z-range around the grain's centre plane
+    phi = O.init_sphere(p, (w["ctr"][0], w["ctr"][1], (nz_slab - 1) / 2.0), w["R"])
+    return p, phi
+
+
+def oracle_slab_for(w, seconds_per_step: float) -> int:
+    """z-thickness of the oracle slab whose one step takes about seconds_per_step."""
+    import oracle as O
+    p, phi = _oracle_slab(w, 2)
+    O.step(p, phi, 1)                      # loads the library, starts the OpenMP pool
+    t0 = time.perf_counter()
+    O.step(p, phi, 1)
+    rate = 2 * w["nx"] * w["ny"] / (time.perf_counter() - t0)
+    return int(max(1, min(w["nz"], rate * seconds_per_step // (w["nx"] * w["ny"]))))
+
+
+def oracle_sample(w, target_s: float = 12.0, steps: int = 3):
+    """FP64 oracle rate (cell-updates/s) on a z-slab of the workload sized for
+    about target_s seconds of host work over `steps` steps."""
+    import oracle as O
+    nz = oracle_slab_for(w, target_s / steps)
+    p, phi = _oracle_slab(w, nz)
+    t0 = time.perf_counter()
+    O.step(p, phi, steps)
+    dt = time.perf_counter() - t0
+    cells = w["nx"] * w["ny"] * nz
+    return cells * steps / dt, nz, dt
+
+
+def cpu_cores():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle as O
+    w = workload(args)
+    # each timed step is one oracle step on a slab sized so that warm-up plus
+    # timed steps take about 90 s of host time
+    nz_slab = oracle_slab_for(w, 90.0 / max(1, args.steps + args.warmup))
+    p, phi = _oracle_slab(w, nz_slab)
+    for _ in range(args.warmup):
+        phi = O.step(p, phi, 1)
+    per_step = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        phi = O.step(p, phi, 1)
+        per_step.append(time.perf_counter() - t0)
+    cells = w["nx"] * w["ny"] * nz_slab
+    tot = sum(per_step)
+    value = cells * args.steps / tot
+    sample = (f"one FP64 oracle step per timed step on a {w['nx']}x{w['ny']}x{nz_slab} z-slab "
+              f"through the grain's centre")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w["name"] + "_ti120_27pt", "grid": [w["nx"], w["ny"], w["nz"]],
+                       "sample_grid": [w["nx"], w["ny"], nz_slab], "stencil": 27,
+                       "scheme": "TI_<120>", "l2": "n/a (host)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------- GPU arm
+
+
+def run_gpu(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_1910_05180_gb300 import spfm as S
+
+    w = workload(args)
+    dtype = {"f32": S.SPFM_F32, "f64": S.SPFM_F64, "bf16": S.SPFM_BF16}[args.dtype]
+    scheme = {"ti120": S.SPFM_TI_GLOBAL, "fd": S.SPFM_FD}[args.scheme]
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        g = S.Grid(w["nx"], w["ny"], w["nz"], dtype=dtype, bc=(S.SPFM_PERIODIC,) * 6, n=w["u"],
+                   center=w["ctr"], stream=stream)
+        g.init_sphere(w["ctr"], w["R"], w["lam"], w["dx"])
+    kw = dict(M=w["M"], Gamma=w["Gamma"], lam=w["lam"], dx=w["dx"], dt=w["dt"], dF=w["dF"],
+              stencil=w["stencil"], scheme=scheme)
+    cells = w["nx"] * w["ny"] * w["nz"]
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for i in range(args.warmup):
+        g.step(1, **kw)
+        if (i + 1) % STATS_EVERY == 0:
+            g.stats()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev.index if dev.index is not None else 0)
+    clocks.start()
+    launches = 0
+    stats_seen = []
+    t_start.record(stream)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        g.step(1, **kw)
+        ev[i][1].record(stream)
+        launches += 1
+        if (i + 1) % STATS_EVERY == 0:
+            stats_seen.append(g.stats())
+            launches += 2
+    t_end.record(stream)
+    barrier()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    kern_ms = [a.elapsed_time(b) for a, b in ev]
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * cells * args.steps / (total_ms / 1e3)
+    avg_kernel_ms = statistics.mean(kern_ms)
+    bpu = BYTES_PER_UPDATE[args.dtype]
+    peak, peak_kind = measured_hbm_peak()
+    achieved = cells * bpu / (avg_kernel_ms / 1e3) / 1e9
+    kernel_key = f"spfm_step_kernel_{args.dtype}_27pt_{args.scheme}_{w['nx']}"
+
+    # end to end through the public API from pinned host memory: upload the
+    # initial field, E2E_STEPS steps, stats, read the field back
+    e2e = None
+    if not args.no_e2e:
+        E2E_STEPS = 50
+        host_in = g.get_field(to_host=True)
+        host_out = torch.empty_like(host_in).pin_memory()
+        iters = 3
+        barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(iters):
+            S.spfm_set_field(g.handle, host_in.data_ptr(), 1)
+            g.step(E2E_STEPS, **kw)
+            g.stats()
+            S.spfm_get_field(g.handle, host_out.data_ptr(), 1)
+        t1.record(stream)
+        barrier()
+        e_ms = t0.elapsed_time(t1)
+        fb = host_in.numel() * host_in.element_size()
+        e2e = {"value": ws * cells * E2E_STEPS * iters / (e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": fb / E2E_STEPS, "d2h_bytes_per_step": (fb + 96) / E2E_STEPS,
+               "note": f"per call: host field in, {E2E_STEPS} steps, stats, host field out"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, nzs, dt = oracle_sample(w)
+        cpu = {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"3 FP64 oracle steps on a {w['nx']}x{w['ny']}x{nzs} z-slab of the "
+                         f"workload ({dt:.1f} s)"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": w["name"] + f"_{args.scheme}_{args.dtype}_27pt",
+                       "grid": [w["nx"], w["ny"], w["nz"]], "stencil": 27,
+                       "scheme": "TI_<120>" if args.scheme == "ti120" else "CF+h3",
+                       "lambda": w["lam"], "dt": w["dt"], "dF": w["dF"], "bc": "periodic",
+                       "stats_every": STATS_EVERY,
+                       "l2": "inputs larger than L2 (two %d MB fields)" % (cells * bpu // 2 // 2**20),
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": profiled_traffic(kernel_key),
+                         "kernel": "spfm_step_kernel", "bytes_per_update": bpu,
+                         "avg_launch_ms": avg_kernel_ms},
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+            "last_stats": stats_seen[-1] if stats_seen else None,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

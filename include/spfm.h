@@ -1,0 +1,158 @@
+/*
+ * spfm.h -- C ABI of the GB300 library for the explicit time step of the
+ * sharp phase-field method (SPFM) and of the conventional finite-difference
+ * (CF) phase-field model, after Fleck, Schleifer, Zimbrod, "Frictionless
+ * motion of diffuse interfaces by sharp phase-field modeling"
+ * (arXiv:1910.05180).
+ *
+ * Model (Sec. 2.1).  On a cubic grid of spacing dx the field phi_p evolves by
+ * the Allen-Cahn relaxation of Eq. 2, 3 lambda Gamma dphi/dt = -2 M dF/dphi,
+ * of the discrete free energy of Eq. 1, summed over the 3, 9 or 13 grid
+ * directions of Tab. 1 (6, 18 or 26 neighbours).  Per cell and step:
+ *
+ *   R_p = sum_k c_k (phi_{p+r_k} + phi_{p-r_k} - 2 phi_p)
+ *         - q s sum_k 4 c_k A_k / (1 - A_k s^2)        (TI, Eqs. 5-6)
+ *           or  - (D/lambda^2)(16/3) sum_k w_k q s    (CF, Tab. 2)
+ *         - (4 M dF / (lambda Gamma)) q                 (h3 driving term)
+ *   phi_p <- phi_p + dt R_p                             (explicit Euler)
+ *
+ * with q = phi(1-phi), s = 1-2phi, D = 2M/(3 C_Gamma), w_k = gamma_j nu_j,
+ * nu_j = 3/m_j, c_k = D w_k / |r_k|^2 and A_k = tanh^2(2 r_k.n / lambda).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an spfm_status; nothing is thrown across the ABI.
+ *    On failure spfm_last_error() holds a one-line message.
+ *  - Device memory is owned by the caller (e.g. allocated through PyTorch).
+ *    The library owns only its opaque host objects and never frees caller
+ *    buffers.  Pointers named `field`, `scratch` and `dst`/`src` with
+ *    *_on_host == 0 are device pointers of the current CUDA device.
+ *  - Field layout in HBM: x fastest, element (i, j, k) at
+ *    field[(k * ny + j) * pitch_x + i], pitch_x = nx rounded up to a multiple
+ *    of 16 bytes worth of elements; every row starts 16-byte aligned.  The
+ *    base pointer must be 16-byte aligned.  Padding elements are never read
+ *    as data.
+ *  - Launches are asynchronous on the grid's stream.  spfm_interface_stats,
+ *    spfm_get_field (to host) and spfm_batch_stats synchronise that stream.
+ */
+#ifndef SPFM_H
+#define SPFM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int spfm_status;
+#define SPFM_OK 0
+#define SPFM_EINVAL (-1)     /* bad argument: sizes, lambda <= 0, |n| != 1, stencil */
+#define SPFM_EUNSTABLE (-2)  /* dt above the explicit-Euler stability bound */
+#define SPFM_EPHASE (-3)     /* CF driving force beyond phase stability, Sec. 3.1 */
+#define SPFM_ECUDA (-4)      /* a CUDA runtime call failed */
+#define SPFM_ENONFINITE (-5) /* the field holds NaN/Inf (reported by the stats) */
+#define SPFM_ETIMEOUT (-6)   /* a bounded device-side wait gave up */
+#define SPFM_ENOMEM (-7)     /* caller-provided scratch is too small */
+
+enum { SPFM_F64 = 0, SPFM_F32 = 1, SPFM_BF16 = 2 };              /* storage type */
+enum { SPFM_PERIODIC = 0, SPFM_NOFLUX = 1, SPFM_CONTACT = 2 };   /* boundary kinds */
+enum { SPFM_TI_GLOBAL = 0, SPFM_TI_LOCAL = 1, SPFM_FD = 2 };     /* schemes */
+enum { SPFM_STATS_ENERGY = 1 };                                  /* stats flags */
+
+typedef struct spfm_grid spfm_grid;
+typedef struct spfm_batch spfm_batch;
+
+typedef struct {
+    int nx, ny, nz;          /* interior cells, each >= 1 */
+    int dtype;               /* SPFM_F64 | SPFM_F32 | SPFM_BF16 (BF16 = storage only) */
+    int bc[6];               /* per face x-, x+, y-, y+, z-, z+; PERIODIC must be paired */
+    double n[3];             /* unit interface normal: TI coupling direction u and the
+                                CONTACT boundary (Eq. 7); planar position estimator */
+    double gamma[3];         /* shell ponderations gamma_1..3; all 0 selects defaults:
+                                (1,0,0), (1/3,2/3,0), (1/2,1/3,1/6) for 6/18/26 */
+    double C_gamma;          /* interface-energy calibration; 0 selects 2/3 */
+    double center[3];        /* centre of the radial position estimator */
+    void *field[2];          /* caller-owned device buffers (ping-pong), field_bytes each */
+    void *scratch;           /* caller-owned device scratch, scratch_bytes (spfm_layout) */
+    size_t scratch_bytes;
+    void *stream;            /* cudaStream_t; NULL = legacy default stream */
+} spfm_grid_desc;
+
+typedef struct {
+    double volume;      /* sum phi dx^3 */
+    double S_w;         /* sum q over the band 1e-6 < phi < 1-1e-6 */
+    double S_c;         /* sum q (p.n - (lambda/2) artanh(1-2phi)) over the band */
+    double S_r;         /* sum q (|p-center| + (lambda/2) artanh(1-2phi)) over the band */
+    double phi_min, phi_max;
+    double nonfinite;   /* number of NaN/Inf cells */
+    double position;    /* S_c / S_w: planar interface position along n (Sec. 2.3) */
+    double radius;      /* S_r / S_w: radius of a grain with phi = 0 inside */
+    double energy;      /* interface energy F_int of Eq. 1 at dF = 0 (SPFM_STATS_ENERGY) */
+    double steps;       /* steps taken since the last init/set_field */
+    double time;        /* simulated time since the last init/set_field */
+} spfm_stats;
+
+/* Per-grid step parameters of a batch (same meaning as in spfm_step). */
+typedef struct {
+    double M, Gamma, lambda, dx, dt, dF;
+    int stencil, scheme;
+} spfm_step_args;
+
+/* Layout of a grid: pitch_x (elements), bytes of ONE field buffer and bytes of
+ * scratch the caller must provide.  Any output pointer may be NULL. */
+spfm_status spfm_layout(const spfm_grid_desc *desc, size_t *pitch_x, size_t *field_bytes,
+                        size_t *scratch_bytes);
+
+/* Validate desc and create the host handle.  The handle borrows the buffers. */
+spfm_status spfm_create_grid(const spfm_grid_desc *desc, spfm_grid **out);
+spfm_status spfm_destroy_grid(spfm_grid *g);
+spfm_status spfm_set_stream(spfm_grid *g, void *stream);
+
+/* Ideal planar profile of Eq. 3, phi = (1 - tanh(2 (p.n - c)/lambda))/2 at
+ * p = dx (i, j, k), with the desc's n.  Computed in FP64, stored in dtype. */
+spfm_status spfm_init_planar(spfm_grid *g, double c, double lambda, double dx);
+/* Radial ideal profile of a grain with phi = 0 inside:
+ * phi = (1 - tanh(2 (R - |p - ctr|)/lambda))/2.  Also sets desc center = ctr. */
+spfm_status spfm_init_sphere(spfm_grid *g, const double ctr[3], double R, double lambda,
+                             double dx);
+
+/* n_steps explicit steps (Eq. 2 with Eq. 1; TI per Eqs. 5-6, TI_n with the
+ * local normal, or CF).  stencil in {6, 18, 26}.  Validates first:
+ * SPFM_EINVAL, SPFM_EUNSTABLE (dt above 2 / bound of the Jacobian's spectral
+ * radius), SPFM_EPHASE (CF and |dF dx/Gamma| >= 8/(3 C_Gamma lambda/dx),
+ * Sec. 3.1).  Asynchronous on the grid's stream. */
+spfm_status spfm_step(spfm_grid *g, int n_steps, double M, double Gamma, double lambda,
+                      double dx, double dt, double dF, int stencil, int scheme);
+
+/* FP64 interface diagnostics of the current field (Sec. 2.3 inversion of the
+ * ideal profile); flags may include SPFM_STATS_ENERGY.  Uses the model of the
+ * last spfm_step (or lambda/dx of the last init).  Synchronises the stream.
+ * Returns SPFM_ENONFINITE (with *out filled) if the field holds NaN/Inf. */
+spfm_status spfm_interface_stats(spfm_grid *g, int flags, spfm_stats *out);
+
+/* Copy the current field to/from a dense (nz, ny, nx) array of the storage
+ * type; *_on_host selects a host or a device pointer. set_field resets steps. */
+spfm_status spfm_get_field(spfm_grid *g, void *dst, int dst_on_host);
+spfm_status spfm_set_field(spfm_grid *g, const void *src, int src_on_host);
+/* Index (0 or 1) of the buffer holding the current field. */
+int spfm_current(const spfm_grid *g);
+
+/* Message of the last failure on g (or of this thread when g is NULL). */
+const char *spfm_last_error(const spfm_grid *g);
+
+/* ---- batches: many grids of one dtype advanced by one launch per step over
+ * a packed tile work-list.  No counterpart in the paper, which advances one
+ * grid at a time; each grid's result is the same as with spfm_step. */
+spfm_status spfm_batch_scratch_bytes(spfm_grid *const *grids, int n, size_t *bytes);
+spfm_status spfm_batch_create(spfm_grid *const *grids, int n, void *scratch,
+                              size_t scratch_bytes, void *stream, spfm_batch **out);
+/* n_steps steps of every grid with its own args[i]; all grids must share stencil and
+ * scheme.  Replays a captured CUDA graph of the per-step launches. */
+spfm_status spfm_batch_step(spfm_batch *b, int n_steps, const spfm_step_args *args);
+/* Diagnostics of every grid in one pass; out has n entries.  Synchronises. */
+spfm_status spfm_batch_stats(spfm_batch *b, int flags, spfm_stats *out);
+spfm_status spfm_batch_destroy(spfm_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

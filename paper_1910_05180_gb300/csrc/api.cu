@@ -1,0 +1,456 @@
+// api.cu -- the C ABI of include/spfm.h: grid handles, validation, host-side
+// FP64 coefficients (a1), and the launches of the step, init and stats kernels.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "spfm_internal.h"
+
+using namespace spfm;
+
+namespace {
+
+thread_local std::string t_err;
+
+}  // namespace
+
+struct spfm_grid {
+    spfm_grid_desc d;
+    GridGeom geom;
+    size_t elem;           // bytes per element
+    int cur = 0;           // buffer holding the current field
+    long long steps = 0;
+    double time = 0.0;
+    // model of the last step (stats: energy, estimator)
+    double M = 1.0, Gamma = 1.0, lambda = 0.0, dx = 1.0, dF = 0.0;
+    int stencil = 26, scheme = SPFM_TI_GLOBAL;
+    std::string err;
+};
+
+namespace spfm_host {
+
+int fail(spfm_grid *g, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (g) g->err = buf;
+    t_err = buf;
+    return code;
+}
+
+int cuda_fail(spfm_grid *g, cudaError_t e, const char *what)
+{
+    return fail(g, SPFM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+size_t elem_size(int dtype)
+{
+    return dtype == SPFM_F64 ? 8 : (dtype == SPFM_F32 ? 4 : 2);
+}
+
+// Model coefficients in FP64 (a1).  gamma defaults, nu_j = 3/m_j, c_j, A_k
+// grouped by value, stability and phase checks.
+struct Model {
+    double gamma[3], w[kMaxTerms], c_shell[3], ck[kMaxTerms];
+    double a[kMaxTerms];
+    int nterms;
+    double beta[kMaxTerms], A[kMaxTerms];
+    double kmu, kappa, D, Cg;
+    double aface[6];
+    double bound;   // upper bound of the spectral radius of the Euler Jacobian
+};
+
+int n_dirs(int stencil) { return stencil == 6 ? 3 : (stencil == 18 ? 9 : 13); }
+
+void default_gamma(int stencil, const double *given, double *g)
+{
+    g[0] = given[0]; g[1] = given[1]; g[2] = given[2];
+    if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0) {
+        if (stencil == 6) { g[0] = 1.0; g[1] = 0.0; g[2] = 0.0; }
+        else if (stencil == 18) { g[0] = 1.0 / 3.0; g[1] = 2.0 / 3.0; g[2] = 0.0; }
+        else { g[0] = 0.5; g[1] = 1.0 / 3.0; g[2] = 1.0 / 6.0; }
+    }
+}
+
+int build_model(spfm_grid *g, double M, double Gamma, double lambda, double dx, double dt,
+                double dF, int stencil, int scheme, Model &m)
+{
+    if (!(M > 0.0) || !(Gamma > 0.0) || !(lambda > 0.0) || !(dx > 0.0) || !(dt > 0.0) ||
+        !isfinite(M) || !isfinite(Gamma) || !isfinite(lambda) || !isfinite(dx) || !isfinite(dt) ||
+        !isfinite(dF))
+        return fail(g, SPFM_EINVAL, "spfm_step: M, Gamma, lambda, dx, dt must be finite and > 0");
+    if (stencil != 6 && stencil != 18 && stencil != 26)
+        return fail(g, SPFM_EINVAL, "spfm_step: stencil %d not in {6, 18, 26}", stencil);
+    if (scheme != SPFM_TI_GLOBAL && scheme != SPFM_TI_LOCAL && scheme != SPFM_FD)
+        return fail(g, SPFM_EINVAL, "spfm_step: unknown scheme %d", scheme);
+    const int nd = n_dirs(stencil);
+    default_gamma(stencil, g->d.gamma, m.gamma);
+    const double nu[3] = {1.0, 0.5, 0.75};   // 3 / m_j, m = (3, 6, 4) directions per shell
+    m.Cg = g->d.C_gamma > 0.0 ? g->d.C_gamma : 2.0 / 3.0;
+    m.D = 2.0 * M / (3.0 * m.Cg);
+    for (int j = 0; j < 3; ++j) {
+        const bool active = (j == 0) || (j == 1 && stencil >= 18) || (j == 2 && stencil == 26);
+        m.c_shell[j] = active ? m.D * m.gamma[j] * nu[j] / ((j + 1) * dx * dx) : 0.0;
+    }
+    double wsum = 0.0;
+    for (int k = 0; k < kMaxTerms; ++k) {
+        const Dir d = grid_dir(k);
+        m.w[k] = k < nd ? m.gamma[d.shell - 1] * nu[d.shell - 1] : 0.0;
+        m.ck[k] = k < nd ? m.c_shell[d.shell - 1] : 0.0;
+        wsum += m.w[k];
+        const double rn = dx * (d.x * g->d.n[0] + d.y * g->d.n[1] + d.z * g->d.n[2]);
+        m.a[k] = tanh(2.0 * rn / lambda);   // Eq. 5
+    }
+    // group equal A_k = a_k^2 of the active directions (TI global)
+    m.nterms = 0;
+    for (int k = 0; k < nd; ++k) {
+        const double A = m.a[k] * m.a[k];
+        const double beta = 4.0 * m.ck[k] * A;
+        if (!(A > 1e-300) || beta == 0.0) continue;
+        int t = 0;
+        for (; t < m.nterms; ++t)
+            if (fabs(m.A[t] - A) <= 4e-15 * A) break;
+        if (t == m.nterms) { m.A[t] = A; m.beta[t] = 0.0; ++m.nterms; }
+        m.beta[t] += beta;
+    }
+    m.kmu = 4.0 * M * dF / (lambda * Gamma);
+    m.kappa = m.D / (lambda * lambda) * (16.0 / 3.0) * wsum;
+    for (int f = 0; f < 6; ++f) {
+        const double sgn = (f % 2 == 0) ? -1.0 : 1.0;
+        m.aface[f] = tanh(2.0 * sgn * dx * g->d.n[f / 2] / lambda);
+    }
+    // Spectral radius of the Laplacian part: its symbol is multilinear in
+    // cos(xi_x), cos(xi_y), cos(xi_z), so the maximum sits on xi in {0, pi}^3.
+    double lap = 0.0;
+    for (int corner = 0; corner < 8; ++corner) {
+        const double cx = (corner & 1) ? -1.0 : 1.0, cy = (corner & 2) ? -1.0 : 1.0,
+                     cz = (corner & 4) ? -1.0 : 1.0;
+        double s = 0.0;
+        for (int k = 0; k < nd; ++k) {
+            const Dir d = grid_dir(k);
+            // cos(xi.d) with xi_i in {0, pi}: product of cos(xi_i)^|d_i|
+            double c = 1.0;
+            if (d.x) c *= cx;
+            if (d.y) c *= cy;
+            if (d.z) c *= cz;
+            s += m.ck[k] * (2.0 - 2.0 * c);
+        }
+        lap = std::max(lap, s);
+    }
+    double pot = 0.0;
+    if (scheme == SPFM_FD) {
+        pot = m.kappa;
+    } else {
+        for (int k = 0; k < nd; ++k) {
+            const Dir d = grid_dir(k);
+            // TI_n: the largest coupling any local normal can give this direction
+            const double amax = scheme == SPFM_TI_LOCAL
+                                    ? tanh(2.0 * dx * sqrt((double)d.shell) / lambda)
+                                    : fabs(m.a[k]);
+            const double A = amax * amax;
+            pot += 4.0 * m.ck[k] * A / (1.0 - A);
+        }
+    }
+    m.bound = lap + pot + fabs(m.kmu);
+    if (dt * m.bound > 2.0)
+        return fail(g, SPFM_EUNSTABLE,
+                    "spfm_step: dt = %g exceeds the explicit-Euler bound 2/%g = %g", dt, m.bound,
+                    2.0 / m.bound);
+    if (scheme == SPFM_FD) {
+        const double lam_t = lambda / dx, dF_t = fabs(dF) * dx / Gamma;
+        const double limit = 8.0 / (3.0 * m.Cg * lam_t);
+        if (dF_t >= limit)
+            return fail(g, SPFM_EPHASE,
+                        "spfm_step: CF driving force |dF dx/Gamma| = %g is beyond phase stability "
+                        "8/(3 C_Gamma lambda/dx) = %g",
+                        dF_t, limit);
+    }
+    return SPFM_OK;
+}
+
+template <class T>
+void fill_coef(const spfm_grid *g, const Model &m, double dt, StepCoef<T> &c)
+{
+    memset(&c, 0, sizeof c);
+    c.g = g->geom;
+    for (int f = 0; f < 6; ++f) c.aface[f] = (T)m.aface[f];
+    c.c1 = (T)m.c_shell[0];
+    c.c2 = (T)m.c_shell[1];
+    c.c3 = (T)m.c_shell[2];
+    c.dt = (T)dt;
+    c.kmu = (T)m.kmu;
+    c.kappa = (T)m.kappa;
+    c.nterms = m.nterms;
+    for (int t = 0; t < kMaxTerms; ++t) {
+        c.beta[t] = t < m.nterms ? (T)m.beta[t] : T(0);
+        c.A[t] = t < m.nterms ? (T)m.A[t] : T(0);
+        c.ck[t] = (T)m.ck[t];
+    }
+}
+
+cudaStream_t stream_of(const spfm_grid *g) { return (cudaStream_t)g->d.stream; }
+
+}  // namespace spfm_host
+
+using namespace spfm_host;
+
+extern "C" {
+
+const char *spfm_last_error(const spfm_grid *g)
+{
+    return g ? g->err.c_str() : t_err.c_str();
+}
+
+spfm_status spfm_layout(const spfm_grid_desc *d, size_t *pitch_x, size_t *field_bytes,
+                        size_t *scratch_bytes)
+{
+    if (!d) return fail(nullptr, SPFM_EINVAL, "spfm_layout: desc is NULL");
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1)
+        return fail(nullptr, SPFM_EINVAL, "spfm_layout: sizes must be >= 1");
+    if (d->dtype != SPFM_F64 && d->dtype != SPFM_F32 && d->dtype != SPFM_BF16)
+        return fail(nullptr, SPFM_EINVAL, "spfm_layout: unknown dtype %d", d->dtype);
+    const size_t es = elem_size(d->dtype), per16 = 16 / es;
+    const size_t px = (d->nx + per16 - 1) / per16 * per16;
+    if (pitch_x) *pitch_x = px;
+    if (field_bytes) *field_bytes = px * (size_t)d->ny * (size_t)d->nz * es;
+    if (scratch_bytes) *scratch_bytes = stats_scratch_bytes();
+    return SPFM_OK;
+}
+
+spfm_status spfm_create_grid(const spfm_grid_desc *d, spfm_grid **out)
+{
+    if (!out) return fail(nullptr, SPFM_EINVAL, "spfm_create_grid: out is NULL");
+    *out = nullptr;
+    size_t px = 0, fb = 0, sb = 0;
+    spfm_status st = spfm_layout(d, &px, &fb, &sb);
+    if (st != SPFM_OK) return st;
+    if ((long long)px * d->ny * (long long)d->nz >= (1LL << 40))
+        return fail(nullptr, SPFM_EINVAL, "spfm_create_grid: grid too large");
+    for (int f = 0; f < 6; ++f)
+        if (d->bc[f] != SPFM_PERIODIC && d->bc[f] != SPFM_NOFLUX && d->bc[f] != SPFM_CONTACT)
+            return fail(nullptr, SPFM_EINVAL, "spfm_create_grid: bad boundary kind on face %d", f);
+    for (int ax = 0; ax < 3; ++ax)
+        if ((d->bc[2 * ax] == SPFM_PERIODIC) != (d->bc[2 * ax + 1] == SPFM_PERIODIC))
+            return fail(nullptr, SPFM_EINVAL, "spfm_create_grid: PERIODIC must be set on both faces of axis %d", ax);
+    const double nn = d->n[0] * d->n[0] + d->n[1] * d->n[1] + d->n[2] * d->n[2];
+    if (!(fabs(nn - 1.0) < 1e-9))
+        return fail(nullptr, SPFM_EINVAL, "spfm_create_grid: |n| = %g, must be 1", sqrt(nn));
+    for (int b = 0; b < 2; ++b)
+        if (!d->field[b] || ((uintptr_t)d->field[b] & 15))
+            return fail(nullptr, SPFM_EINVAL, "spfm_create_grid: field[%d] NULL or not 16-byte aligned", b);
+    if (d->field[0] == d->field[1])
+        return fail(nullptr, SPFM_EINVAL, "spfm_create_grid: the two field buffers must differ");
+    if (!d->scratch || ((uintptr_t)d->scratch & 15) || d->scratch_bytes < sb)
+        return fail(nullptr, SPFM_ENOMEM, "spfm_create_grid: scratch NULL, unaligned or below %zu bytes", sb);
+    if (d->C_gamma < 0.0 || d->gamma[0] < 0.0 || d->gamma[1] < 0.0 || d->gamma[2] < 0.0)
+        return fail(nullptr, SPFM_EINVAL, "spfm_create_grid: negative gamma or C_gamma");
+    spfm_grid *g = new spfm_grid();
+    g->d = *d;
+    g->elem = elem_size(d->dtype);
+    g->geom.nx = d->nx;
+    g->geom.ny = d->ny;
+    g->geom.nz = d->nz;
+    g->geom.pitch = (int)px;
+    g->geom.plane = (long long)px * d->ny;
+    for (int f = 0; f < 6; ++f) g->geom.bc[f] = d->bc[f];
+    *out = g;
+    return SPFM_OK;
+}
+
+spfm_status spfm_destroy_grid(spfm_grid *g)
+{
+    delete g;
+    return SPFM_OK;
+}
+
+spfm_status spfm_set_stream(spfm_grid *g, void *stream)
+{
+    if (!g) return fail(nullptr, SPFM_EINVAL, "spfm_set_stream: grid is NULL");
+    g->d.stream = stream;
+    return SPFM_OK;
+}
+
+int spfm_current(const spfm_grid *g) { return g ? g->cur : -1; }
+
+static spfm_status init_common(spfm_grid *g, InitArgs &a, double lambda, double dx)
+{
+    if (!(lambda > 0.0) || !(dx > 0.0))
+        return fail(g, SPFM_EINVAL, "spfm_init: lambda and dx must be > 0");
+    a.g = g->geom;
+    a.dtype = g->d.dtype;
+    a.lambda = lambda;
+    a.dx = dx;
+    g->cur = 0;
+    cudaError_t e = launch_init(a, g->d.field[0], stream_of(g));
+    if (e != cudaSuccess) return cuda_fail(g, e, "spfm_init");
+    g->steps = 0;
+    g->time = 0.0;
+    g->lambda = lambda;
+    g->dx = dx;
+    return SPFM_OK;
+}
+
+spfm_status spfm_init_planar(spfm_grid *g, double c, double lambda, double dx)
+{
+    if (!g) return fail(nullptr, SPFM_EINVAL, "spfm_init_planar: grid is NULL");
+    InitArgs a;
+    memset(&a, 0, sizeof a);
+    for (int i = 0; i < 3; ++i) a.n[i] = g->d.n[i];
+    a.c = c;
+    return init_common(g, a, lambda, dx);
+}
+
+spfm_status spfm_init_sphere(spfm_grid *g, const double ctr[3], double R, double lambda, double dx)
+{
+    if (!g || !ctr) return fail(g, SPFM_EINVAL, "spfm_init_sphere: NULL argument");
+    InitArgs a;
+    memset(&a, 0, sizeof a);
+    a.sphere = 1;
+    for (int i = 0; i < 3; ++i) { a.ctr[i] = ctr[i]; g->d.center[i] = ctr[i]; }
+    a.R = R;
+    return init_common(g, a, lambda, dx);
+}
+
+spfm_status spfm_step(spfm_grid *g, int n_steps, double M, double Gamma, double lambda, double dx,
+                      double dt, double dF, int stencil, int scheme)
+{
+    if (!g) return fail(nullptr, SPFM_EINVAL, "spfm_step: grid is NULL");
+    if (n_steps < 0) return fail(g, SPFM_EINVAL, "spfm_step: n_steps < 0");
+    Model m;
+    spfm_status st = build_model(g, M, Gamma, lambda, dx, dt, dF, stencil, scheme, m);
+    if (st != SPFM_OK) return st;
+    if (scheme == SPFM_TI_LOCAL)
+        return fail(g, SPFM_EINVAL, "spfm_step: SPFM_TI_LOCAL is not available in this build");
+    const LaunchCfg cfg{stencil, scheme};
+    cudaStream_t s = stream_of(g);
+    if (g->d.dtype == SPFM_F64) {
+        StepCoef<double> c;
+        fill_coef<double>(g, m, dt, c);
+        for (int i = 0; i < n_steps; ++i) {
+            cudaError_t e = launch_step_f64(c, (const double *)g->d.field[g->cur],
+                                            (double *)g->d.field[1 - g->cur], cfg, s);
+            if (e != cudaSuccess) return cuda_fail(g, e, "spfm_step");
+            g->cur ^= 1;
+        }
+    } else {
+        StepCoef<float> c;
+        fill_coef<float>(g, m, dt, c);
+        for (int i = 0; i < n_steps; ++i) {
+            cudaError_t e;
+            if (g->d.dtype == SPFM_F32)
+                e = launch_step_f32(c, (const float *)g->d.field[g->cur], (float *)g->d.field[1 - g->cur], cfg, s);
+            else
+                e = launch_step_bf16(c, (const __nv_bfloat16 *)g->d.field[g->cur],
+                                     (__nv_bfloat16 *)g->d.field[1 - g->cur], cfg, s);
+            if (e != cudaSuccess) return cuda_fail(g, e, "spfm_step");
+            g->cur ^= 1;
+        }
+    }
+    g->steps += n_steps;
+    g->time += n_steps * dt;
+    g->M = M;
+    g->Gamma = Gamma;
+    g->lambda = lambda;
+    g->dx = dx;
+    g->dF = dF;
+    g->stencil = stencil;
+    g->scheme = scheme;
+    return SPFM_OK;
+}
+
+spfm_status spfm_interface_stats(spfm_grid *g, int flags, spfm_stats *out)
+{
+    if (!g || !out) return fail(g, SPFM_EINVAL, "spfm_interface_stats: NULL argument");
+    if (!(g->lambda > 0.0)) return fail(g, SPFM_EINVAL, "spfm_interface_stats: no model yet (init or step first)");
+    StatsArgs a;
+    memset(&a, 0, sizeof a);
+    a.g = g->geom;
+    a.dtype = g->d.dtype;
+    for (int i = 0; i < 3; ++i) { a.n[i] = g->d.n[i]; a.ctr[i] = g->d.center[i]; }
+    a.lambda = g->lambda;
+    a.dx = g->dx;
+    a.energy = (flags & SPFM_STATS_ENERGY) && g->scheme != SPFM_TI_LOCAL ? 1 : 0;
+    a.scheme = g->scheme;
+    a.stencil = g->stencil;
+    a.Gamma = g->Gamma;
+    a.C_gamma = g->d.C_gamma > 0.0 ? g->d.C_gamma : 2.0 / 3.0;
+    double gam[3];
+    default_gamma(g->stencil, g->d.gamma, gam);
+    const double nu[3] = {1.0, 0.5, 0.75};
+    const int nd = n_dirs(g->stencil);
+    for (int k = 0; k < kMaxTerms; ++k) {
+        const Dir d = grid_dir(k);
+        a.w[k] = k < nd ? gam[d.shell - 1] * nu[d.shell - 1] : 0.0;
+        a.a[k] = tanh(2.0 * g->dx * (d.x * g->d.n[0] + d.y * g->d.n[1] + d.z * g->d.n[2]) / g->lambda);
+    }
+    for (int f = 0; f < 6; ++f) {
+        const double sgn = (f % 2 == 0) ? -1.0 : 1.0;
+        a.aface[f] = tanh(2.0 * sgn * g->dx * g->d.n[f / 2] / g->lambda);
+    }
+    double *partials = (double *)g->d.scratch;
+    double *fin = partials + (size_t)kNStat * kStatsBlocks;
+    cudaStream_t s = stream_of(g);
+    cudaError_t e = launch_stats(a, g->d.field[g->cur], partials, fin, s);
+    if (e != cudaSuccess) return cuda_fail(g, e, "spfm_interface_stats");
+    double h[kNStat];
+    e = cudaMemcpyAsync(h, fin, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(g, e, "spfm_interface_stats");
+    out->volume = h[0] * g->dx * g->dx * g->dx;
+    out->S_w = h[1];
+    out->S_c = h[2];
+    out->S_r = h[3];
+    out->phi_min = h[4];
+    out->phi_max = h[5];
+    out->nonfinite = h[6];
+    out->position = h[1] > 0.0 ? h[2] / h[1] : NAN;
+    out->radius = h[1] > 0.0 ? h[3] / h[1] : NAN;
+    out->energy = a.energy ? h[7] * g->dx * g->dx * g->dx : NAN;
+    out->steps = (double)g->steps;
+    out->time = g->time;
+    if (h[6] > 0.0) return fail(g, SPFM_ENONFINITE, "field holds %.0f non-finite cells", h[6]);
+    return SPFM_OK;
+}
+
+static spfm_status copy_field(spfm_grid *g, void *host_or_dev, int on_host, int to_grid)
+{
+    const size_t es = g->elem;
+    const size_t row = (size_t)g->d.nx * es, pitch = (size_t)g->geom.pitch * es;
+    const size_t rows = (size_t)g->d.ny * g->d.nz;
+    cudaStream_t s = stream_of(g);
+    cudaError_t e;
+    if (to_grid) {
+        e = cudaMemcpy2DAsync(g->d.field[g->cur], pitch, host_or_dev, row, row, rows,
+                              on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s);
+    } else {
+        e = cudaMemcpy2DAsync(host_or_dev, row, g->d.field[g->cur], pitch, row, rows,
+                              on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s);
+    }
+    if (e == cudaSuccess && on_host) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(g, e, to_grid ? "spfm_set_field" : "spfm_get_field");
+    return SPFM_OK;
+}
+
+spfm_status spfm_get_field(spfm_grid *g, void *dst, int dst_on_host)
+{
+    if (!g || !dst) return fail(g, SPFM_EINVAL, "spfm_get_field: NULL argument");
+    return copy_field(g, dst, dst_on_host, 0);
+}
+
+spfm_status spfm_set_field(spfm_grid *g, const void *src, int src_on_host)
+{
+    if (!g || !src) return fail(g, SPFM_EINVAL, "spfm_set_field: NULL argument");
+    spfm_status st = copy_field(g, const_cast<void *>(src), src_on_host, 1);
+    if (st == SPFM_OK) { g->steps = 0; g->time = 0.0; }
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,143 @@
+// spfm_internal.h -- shared definitions of the GB300 SPFM library (host + device).
+//
+// Parameter blocks handed to the kernels, the boundary-aware element loader
+// (periodic / no-flux / contact-angle ghosts, Eq. 7), and the launcher
+// declarations that connect the C ABI (api.cu) to the kernels.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/spfm.h"
+
+namespace spfm {
+
+constexpr int kMaxTerms = 13;    // grid directions of the 26-neighbour stencil (Tab. 1)
+constexpr int kStatsBlocks = 608;  // 4 x 152 SMs; fixed so the reduction order is fixed
+constexpr int kNStat = 12;       // doubles per partial (see stats.cu)
+
+// Grid vectors of Tab. 1, one per +/- pair: shell 1 (k = 0..2), shell 2
+// (3..8), shell 3 (9..12).
+struct Dir { int x, y, z, shell; };
+__host__ __device__ inline Dir grid_dir(int k)
+{
+    switch (k) {
+    case 0: return {1, 0, 0, 1};
+    case 1: return {0, 1, 0, 1};
+    case 2: return {0, 0, 1, 1};
+    case 3: return {1, 1, 0, 2};
+    case 4: return {0, 1, 1, 2};
+    case 5: return {1, 0, 1, 2};
+    case 6: return {1, -1, 0, 2};
+    case 7: return {0, 1, -1, 2};
+    case 8: return {1, 0, -1, 2};
+    case 9: return {1, 1, 1, 3};
+    case 10: return {-1, 1, 1, 3};
+    case 11: return {1, -1, 1, 3};
+    default: return {1, 1, -1, 3};
+    }
+}
+
+// Geometry of one grid as the kernels see it.
+struct GridGeom {
+    int nx, ny, nz;
+    int pitch;          // elements per row (16-byte multiple)
+    long long plane;    // pitch * ny
+    int bc[6];          // SPFM_PERIODIC / NOFLUX / CONTACT per face
+};
+
+// Step coefficients of one grid, precomputed on the host in FP64 (a1) and
+// rounded to the compute type T.
+template <class T>
+struct StepCoef {
+    GridGeom g;
+    T aface[6];             // signed contact coupling per face, tanh(2 (x_g - x_s).n / lambda)
+    T c1, c2, c3;           // Laplacian shell coefficients D w_j / |r_j|^2
+    T dt, kmu, kappa;       // Euler step, h3 driving 4 M dF/(lambda Gamma), CF potential
+    int nterms;             // TI: distinct non-zero A_k after grouping
+    T beta[kMaxTerms];      // TI: summed 4 c_k A_k of each group
+    T A[kMaxTerms];         // TI: the group's A_k = a_k^2
+    // TI_n (local normal): per-direction c_k, (lambda/2), 1/(2 dx), 2 dx/lambda, clamp
+    T ck[kMaxTerms];
+    T half_lam, inv_2dx, two_dx_over_lam, eps;
+};
+
+// Ghost mapping for one axis: at most one cell outside [0, n).  Returns the
+// source coordinate and sets *contact when a contact-angle transform applies.
+__host__ __device__ inline int map_axis(int c, int n, int bc_lo, int bc_hi, int *face_hit,
+                                        int face_lo)
+{
+    *face_hit = -1;
+    if (c < 0) {
+        if (bc_lo == SPFM_PERIODIC) return c + n;
+        if (bc_lo == SPFM_CONTACT) *face_hit = face_lo;
+        return 0;
+    }
+    if (c >= n) {
+        if (bc_hi == SPFM_PERIODIC) return c - n;
+        if (bc_hi == SPFM_CONTACT) *face_hit = face_lo + 1;
+        return n - 1;
+    }
+    return c;
+}
+
+// Eq. 7 with a signed coupling a: value at a ghost displaced from its source.
+template <class T>
+__host__ __device__ inline T contact_shift(T v, T a)
+{
+    return (T(1) - a) * v / (T(1) - a * (T(2) * v - T(1)));
+}
+
+template <class S> __host__ __device__ inline float to_f(S v);
+template <> __host__ __device__ inline float to_f<float>(float v) { return v; }
+template <> __host__ __device__ inline float to_f<__nv_bfloat16>(__nv_bfloat16 v)
+{
+    return __bfloat162float(v);
+}
+
+// ---------------------------------------------------------------- launchers
+
+struct LaunchCfg {
+    int stencil;   // 6, 18, 26
+    int scheme;    // SPFM_TI_GLOBAL, SPFM_TI_LOCAL, SPFM_FD
+};
+
+// One explicit step src -> dst of one grid (step_f32.cu / step_f64.cu / step_bf16.cu).
+cudaError_t launch_step_f32(const StepCoef<float> &c, const float *src, float *dst,
+                            LaunchCfg cfg, cudaStream_t st);
+cudaError_t launch_step_f64(const StepCoef<double> &c, const double *src, double *dst,
+                            LaunchCfg cfg, cudaStream_t st);
+cudaError_t launch_step_bf16(const StepCoef<float> &c, const __nv_bfloat16 *src,
+                             __nv_bfloat16 *dst, LaunchCfg cfg, cudaStream_t st);
+
+// Initial ideal profiles and FP64 diagnostics (stats.cu).
+struct InitArgs {
+    GridGeom g;
+    int dtype;
+    int sphere;           // 0 planar (n, c), 1 radial (ctr, R)
+    double n[3], c;
+    double ctr[3], R;
+    double lambda, dx;
+};
+cudaError_t launch_init(const InitArgs &a, void *field, cudaStream_t st);
+
+struct StatsArgs {
+    GridGeom g;
+    int dtype;
+    double n[3], ctr[3];
+    double aface[6];      // contact coupling per face (ghosts of the forward differences)
+    double lambda, dx;
+    int energy;           // 1: also accumulate the interface energy
+    int scheme, stencil;  // energy model
+    double Gamma, C_gamma;
+    double w[kMaxTerms];  // w_k = gamma_j nu_j (0 where inactive)
+    double a[kMaxTerms];  // TI coupling a_k(n)
+};
+// Writes kNStat doubles of the final reduction to final_out (device).
+cudaError_t launch_stats(const StatsArgs &a, const void *field, double *partials,
+                         double *final_out, cudaStream_t st);
+
+size_t stats_scratch_bytes();
+
+}  // namespace spfm

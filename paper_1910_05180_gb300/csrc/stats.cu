@@ -1,0 +1,217 @@
+// stats.cu -- ideal-profile initialisation and FP64 interface diagnostics.
+//
+// init: Eq. 3 (planar) or its radial form, evaluated in FP64 per cell and
+// rounded once to the storage type; padding elements are zeroed.
+//
+// stats: one pass over the field accumulating in FP64, per thread in a fixed
+// grid-stride order, then warp-shuffle and shared-memory block reductions into
+// kStatsBlocks partials, then one CTA reducing the partials in a fixed order,
+// so the result is bit-reproducible for a given grid size.  Sums over the band
+// 1e-6 < phi < 1 - 1e-6 invert the ideal profile (Sec. 2.3):
+//   position  c = sum q (p.n - (lambda/2) artanh(1-2phi)) / sum q
+//   radius    R = sum q (|p - ctr| + (lambda/2) artanh(1-2phi)) / sum q
+// The optional interface energy is Eq. 1 at dF = 0 with forward differences
+// whose ghosts follow the boundary conditions.
+#include <math.h>
+
+#include "spfm_internal.h"
+
+namespace spfm {
+
+template <class S> __device__ __forceinline__ double rd(const S *f, long long i);
+template <> __device__ __forceinline__ double rd<double>(const double *f, long long i) { return f[i]; }
+template <> __device__ __forceinline__ double rd<float>(const float *f, long long i) { return (double)f[i]; }
+template <> __device__ __forceinline__ double rd<__nv_bfloat16>(const __nv_bfloat16 *f, long long i)
+{
+    return (double)__bfloat162float(f[i]);
+}
+
+template <class S> __device__ __forceinline__ S wr(double v);
+template <> __device__ __forceinline__ double wr<double>(double v) { return v; }
+template <> __device__ __forceinline__ float wr<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 wr<__nv_bfloat16>(double v)
+{
+    return __float2bfloat16_rn((float)v);
+}
+
+template <class S>
+__global__ void init_kernel(const InitArgs a, S *f)
+{
+    const long long total = a.g.plane * a.g.nz;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx % a.g.pitch);
+        const long long row = idx / a.g.pitch;
+        const int j = (int)(row % a.g.ny);
+        const int k = (int)(row / a.g.ny);
+        double v = 0.0;
+        if (i < a.g.nx) {
+            const double px = a.dx * i, py = a.dx * j, pz = a.dx * k;
+            if (a.sphere) {
+                const double rx = px - a.ctr[0], ry = py - a.ctr[1], rz = pz - a.ctr[2];
+                const double r = sqrt(rx * rx + ry * ry + rz * rz);
+                v = 0.5 * (1.0 - tanh(2.0 * (a.R - r) / a.lambda));
+            } else {
+                const double pn = px * a.n[0] + py * a.n[1] + pz * a.n[2];
+                v = 0.5 * (1.0 - tanh(2.0 * (pn - a.c) / a.lambda));
+            }
+        }
+        f[idx] = wr<S>(v);
+    }
+}
+
+cudaError_t launch_init(const InitArgs &a, void *field, cudaStream_t st)
+{
+    const long long total = a.g.plane * a.g.nz;
+    long long blocks = (total + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (a.dtype == SPFM_F64) init_kernel<double><<<(int)blocks, 256, 0, st>>>(a, (double *)field);
+    else if (a.dtype == SPFM_F32) init_kernel<float><<<(int)blocks, 256, 0, st>>>(a, (float *)field);
+    else init_kernel<__nv_bfloat16><<<(int)blocks, 256, 0, st>>>(a, (__nv_bfloat16 *)field);
+    return cudaGetLastError();
+}
+
+// element with boundary ghosts (one cell outside per axis), FP64
+template <class S>
+__device__ double ghost_value(const StatsArgs &a, const S *f, int x, int y, int z)
+{
+    int fx, fy, fz;
+    const int sx = map_axis(x, a.g.nx, a.g.bc[0], a.g.bc[1], &fx, 0);
+    const int sy = map_axis(y, a.g.ny, a.g.bc[2], a.g.bc[3], &fy, 2);
+    const int sz = map_axis(z, a.g.nz, a.g.bc[4], a.g.bc[5], &fz, 4);
+    double v = rd<S>(f, (long long)sz * a.g.plane + (long long)sy * a.g.pitch + sx);
+    if (fx >= 0) v = contact_shift<double>(v, a.aface[fx]);
+    if (fy >= 0) v = contact_shift<double>(v, a.aface[fy]);
+    if (fz >= 0) v = contact_shift<double>(v, a.aface[fz]);
+    return v;
+}
+
+// Eq. 6 (TI) or the CF quartic per direction; lam2_r2 = lambda^2/|r_k|^2
+__device__ __forceinline__ double potential(double phi, double a, double lam2_r2, int cf)
+{
+    const double q = phi * (1.0 - phi), s = 1.0 - 2.0 * phi;
+    if (cf) return 8.0 * q * q / 3.0;
+    const double A = a * a;
+    if (A < 1e-8) return lam2_r2 * 2.0 * A * q * q;
+    return lam2_r2 * (q + (1.0 - A) / (4.0 * A) * log((1.0 - A) / (1.0 - A * s * s)));
+}
+
+__device__ __forceinline__ void warp_reduce(double *v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int i = 0; i < kNStat; ++i) {
+            const double o = __shfl_down_sync(0xffffffffu, v[i], off);
+            if (i == 4) v[i] = fmin(v[i], o);
+            else if (i == 5) v[i] = fmax(v[i], o);
+            else v[i] += o;
+        }
+    }
+}
+
+__device__ __forceinline__ void block_reduce_store(double *v, double *out)
+{
+    __shared__ double sm[32][kNStat];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    warp_reduce(v);
+    if (lane == 0)
+        for (int i = 0; i < kNStat; ++i) sm[warp][i] = v[i];
+    __syncthreads();
+    if (warp == 0) {
+        for (int i = 0; i < kNStat; ++i)
+            v[i] = lane < nw ? sm[lane][i] : (i == 4 ? INFINITY : (i == 5 ? -INFINITY : 0.0));
+        warp_reduce(v);
+        if (lane == 0)
+            for (int i = 0; i < kNStat; ++i) out[i] = v[i];
+    }
+}
+
+template <class S>
+__global__ void __launch_bounds__(256) stats_kernel(const StatsArgs a, const S *f, double *partials)
+{
+    double v[kNStat];
+#pragma unroll
+    for (int i = 0; i < kNStat; ++i) v[i] = 0.0;
+    v[4] = INFINITY;
+    v[5] = -INFINITY;
+    const long long cells = (long long)a.g.nx * a.g.ny * a.g.nz;
+    const double e_pref = a.Gamma / (a.C_gamma * a.lambda);
+    const int nd = a.stencil == 6 ? 3 : (a.stencil == 18 ? 9 : 13);
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < cells;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx % a.g.nx);
+        const long long r = idx / a.g.nx;
+        const int j = (int)(r % a.g.ny);
+        const int k = (int)(r / a.g.ny);
+        const double ph = rd<S>(f, (long long)k * a.g.plane + (long long)j * a.g.pitch + i);
+        if (!isfinite(ph)) { v[6] += 1.0; continue; }
+        v[0] += ph;
+        v[4] = fmin(v[4], ph);
+        v[5] = fmax(v[5], ph);
+        if (ph > 1e-6 && ph < 1.0 - 1e-6) {
+            const double q = ph * (1.0 - ph);
+            const double psi = 0.5 * a.lambda * atanh(1.0 - 2.0 * ph);
+            const double px = a.dx * i, py = a.dx * j, pz = a.dx * k;
+            const double pn = px * a.n[0] + py * a.n[1] + pz * a.n[2];
+            const double rx = px - a.ctr[0], ry = py - a.ctr[1], rz = pz - a.ctr[2];
+            v[1] += q;
+            v[2] += q * (pn - psi);
+            v[3] += q * (sqrt(rx * rx + ry * ry + rz * rz) + psi);
+        }
+        if (a.energy) {
+            double e = 0.0;
+            for (int kk = 0; kk < nd; ++kk) {
+                const Dir d = grid_dir(kk);
+                const double r2 = (double)d.shell * a.dx * a.dx;
+                const double nb = ghost_value<S>(a, f, i + d.x, j + d.y, k + d.z);
+                const double dp = nb - ph;
+                e += a.w[kk] * (0.5 * a.lambda * a.lambda * dp * dp / r2 +
+                                potential(ph, a.a[kk], a.lambda * a.lambda / r2, a.scheme == SPFM_FD));
+            }
+            v[7] += e_pref * e;
+        }
+    }
+    block_reduce_store(v, partials + (long long)blockIdx.x * kNStat);
+}
+
+__global__ void __launch_bounds__(256) stats_final_kernel(const double *partials, int nblocks, double *out)
+{
+    double v[kNStat];
+#pragma unroll
+    for (int i = 0; i < kNStat; ++i) v[i] = 0.0;
+    v[4] = INFINITY;
+    v[5] = -INFINITY;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < kNStat; ++i) {
+            const double x = partials[(long long)b * kNStat + i];
+            if (i == 4) v[i] = fmin(v[i], x);
+            else if (i == 5) v[i] = fmax(v[i], x);
+            else v[i] += x;
+        }
+    }
+    block_reduce_store(v, out);
+}
+
+size_t stats_scratch_bytes()
+{
+    return sizeof(double) * (size_t)kNStat * (kStatsBlocks + 1);
+}
+
+cudaError_t launch_stats(const StatsArgs &a, const void *field, double *partials, double *final_out,
+                         cudaStream_t st)
+{
+    if (a.dtype == SPFM_F64)
+        stats_kernel<double><<<kStatsBlocks, 256, 0, st>>>(a, (const double *)field, partials);
+    else if (a.dtype == SPFM_F32)
+        stats_kernel<float><<<kStatsBlocks, 256, 0, st>>>(a, (const float *)field, partials);
+    else
+        stats_kernel<__nv_bfloat16><<<kStatsBlocks, 256, 0, st>>>(a, (const __nv_bfloat16 *)field, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    stats_final_kernel<<<1, 256, 0, st>>>(partials, kStatsBlocks, final_out);
+    return cudaGetLastError();
+}
+
+}  // namespace spfm

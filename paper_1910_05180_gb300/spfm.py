@@ -1,0 +1,259 @@
+"""Thin Python binding of the C ABI in include/spfm.h.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``_build/libspfm_gb300.so``.  PyTorch supplies device memory and the
+CUDA stream.  Importing this module does not build anything; loading the
+library fails loudly when it has not been built (there is no CPU fallback).
+
+The functions keep the C names (``spfm_create_grid``, ``spfm_step``,
+``spfm_interface_stats`` ...).  ``Grid`` bundles a handle with the torch
+buffers it borrows so they stay alive as long as the handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libspfm_gb300.so")
+
+SPFM_OK, SPFM_EINVAL, SPFM_EUNSTABLE, SPFM_EPHASE = 0, -1, -2, -3
+SPFM_ECUDA, SPFM_ENONFINITE, SPFM_ETIMEOUT, SPFM_ENOMEM = -4, -5, -6, -7
+SPFM_F64, SPFM_F32, SPFM_BF16 = 0, 1, 2
+SPFM_PERIODIC, SPFM_NOFLUX, SPFM_CONTACT = 0, 1, 2
+SPFM_TI_GLOBAL, SPFM_TI_LOCAL, SPFM_FD = 0, 1, 2
+SPFM_STATS_ENERGY = 1
+
+TORCH_DTYPE = {SPFM_F64: torch.float64, SPFM_F32: torch.float32, SPFM_BF16: torch.bfloat16}
+STATUS_NAME = {0: "SPFM_OK", -1: "SPFM_EINVAL", -2: "SPFM_EUNSTABLE", -3: "SPFM_EPHASE",
+               -4: "SPFM_ECUDA", -5: "SPFM_ENONFINITE", -6: "SPFM_ETIMEOUT", -7: "SPFM_ENOMEM"}
+
+
+class SpfmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAME.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("dtype", ctypes.c_int),
+        ("bc", ctypes.c_int * 6),
+        ("n", ctypes.c_double * 3),
+        ("gamma", ctypes.c_double * 3),
+        ("C_gamma", ctypes.c_double),
+        ("center", ctypes.c_double * 3),
+        ("field", ctypes.c_void_p * 2),
+        ("scratch", ctypes.c_void_p),
+        ("scratch_bytes", ctypes.c_size_t),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in (
+        "volume", "S_w", "S_c", "S_r", "phi_min", "phi_max", "nonfinite", "position",
+        "radius", "energy", "steps", "time")]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class StepArgs(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_double), ("Gamma", ctypes.c_double), ("lam", ctypes.c_double),
+                ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("dF", ctypes.c_double),
+                ("stencil", ctypes.c_int), ("scheme", ctypes.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+# (name, restype, argtypes) of every exported entry point of include/spfm.h
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+SIGNATURES = [
+    ("spfm_layout", _I, [ctypes.POINTER(GridDesc), ctypes.POINTER(ctypes.c_size_t),
+                         ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+    ("spfm_create_grid", _I, [ctypes.POINTER(GridDesc), ctypes.POINTER(_P)]),
+    ("spfm_destroy_grid", _I, [_P]),
+    ("spfm_set_stream", _I, [_P, _P]),
+    ("spfm_init_planar", _I, [_P, _D, _D, _D]),
+    ("spfm_init_sphere", _I, [_P, ctypes.POINTER(_D), _D, _D, _D]),
+    ("spfm_step", _I, [_P, _I, _D, _D, _D, _D, _D, _D, _I, _I]),
+    ("spfm_interface_stats", _I, [_P, _I, ctypes.POINTER(Stats)]),
+    ("spfm_get_field", _I, [_P, _P, _I]),
+    ("spfm_set_field", _I, [_P, _P, _I]),
+    ("spfm_current", _I, [_P]),
+    ("spfm_last_error", ctypes.c_char_p, [_P]),
+    ("spfm_batch_scratch_bytes", _I, [ctypes.POINTER(_P), _I, ctypes.POINTER(ctypes.c_size_t)]),
+    ("spfm_batch_create", _I, [ctypes.POINTER(_P), _I, _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
+    ("spfm_batch_step", _I, [_P, _I, ctypes.POINTER(StepArgs)]),
+    ("spfm_batch_stats", _I, [_P, _I, ctypes.POINTER(Stats)]),
+    ("spfm_batch_destroy", _I, [_P]),
+]
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(
+                    f"SPFM CUDA library not built ({path}); run paper_1910_05180_gb300.build.build()")
+            lib = ctypes.CDLL(path)
+            for name, res, args in SIGNATURES:
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(status: int, handle=None):
+    if status != SPFM_OK:
+        msg = load().spfm_last_error(handle)
+        raise SpfmError(status, msg.decode() if msg else "")
+    return status
+
+
+# ------------------------------------------------------------- C-named calls
+
+def spfm_layout(desc: GridDesc):
+    px, fb, sb = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    _check(load().spfm_layout(ctypes.byref(desc), ctypes.byref(px), ctypes.byref(fb), ctypes.byref(sb)))
+    return px.value, fb.value, sb.value
+
+
+def spfm_create_grid(desc: GridDesc):
+    h = ctypes.c_void_p()
+    _check(load().spfm_create_grid(ctypes.byref(desc), ctypes.byref(h)))
+    return h
+
+
+def spfm_destroy_grid(h):
+    _check(load().spfm_destroy_grid(h))
+
+
+def spfm_set_stream(h, stream):
+    _check(load().spfm_set_stream(h, stream), h)
+
+
+def spfm_init_planar(h, c, lam, dx):
+    _check(load().spfm_init_planar(h, c, lam, dx), h)
+
+
+def spfm_init_sphere(h, ctr, R, lam, dx):
+    arr = (ctypes.c_double * 3)(*ctr)
+    _check(load().spfm_init_sphere(h, arr, R, lam, dx), h)
+
+
+def spfm_step(h, n_steps, M, Gamma, lam, dx, dt, dF, stencil, scheme):
+    _check(load().spfm_step(h, int(n_steps), M, Gamma, lam, dx, dt, dF, int(stencil), int(scheme)), h)
+
+
+def spfm_interface_stats(h, flags=0, allow_nonfinite=False) -> dict:
+    st = Stats()
+    s = load().spfm_interface_stats(h, int(flags), ctypes.byref(st))
+    if not (allow_nonfinite and s == SPFM_ENONFINITE):
+        _check(s, h)
+    return st.as_dict()
+
+
+def spfm_get_field(h, ptr, on_host):
+    _check(load().spfm_get_field(h, ptr, int(on_host)), h)
+
+
+def spfm_set_field(h, ptr, on_host):
+    _check(load().spfm_set_field(h, ptr, int(on_host)), h)
+
+
+def spfm_current(h) -> int:
+    return load().spfm_current(h)
+
+
+def spfm_last_error(h=None) -> str:
+    m = load().spfm_last_error(h)
+    return m.decode() if m else ""
+
+
+# ------------------------------------------------------------------ helpers
+
+class Grid:
+    """One grid: a handle plus the torch buffers (two fields, scratch) it borrows."""
+
+    def __init__(self, nx, ny, nz, dtype=SPFM_F32, bc=(SPFM_PERIODIC,) * 6, n=(1.0, 0.0, 0.0),
+                 gamma=(0.0, 0.0, 0.0), C_gamma=0.0, center=(0.0, 0.0, 0.0), device="cuda",
+                 stream=None):
+        d = GridDesc()
+        d.nx, d.ny, d.nz, d.dtype = int(nx), int(ny), int(nz), int(dtype)
+        for i in range(6):
+            d.bc[i] = int(bc[i])
+        for i in range(3):
+            d.n[i], d.gamma[i], d.center[i] = float(n[i]), float(gamma[i]), float(center[i])
+        d.C_gamma = float(C_gamma)
+        pitch, fbytes, sbytes = spfm_layout(d)
+        self.pitch, self.field_bytes, self.scratch_bytes = pitch, fbytes, sbytes
+        tdt = TORCH_DTYPE[dtype]
+        self.shape = (int(nz), int(ny), int(nx))
+        self.fields = [torch.zeros((nz, ny, pitch), dtype=tdt, device=device) for _ in range(2)]
+        self.scratch = torch.empty(max(sbytes, 16), dtype=torch.uint8, device=device)
+        for b in range(2):
+            d.field[b] = self.fields[b].data_ptr()
+        d.scratch = self.scratch.data_ptr()
+        d.scratch_bytes = self.scratch.numel()
+        st = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = st
+        d.stream = st.cuda_stream
+        self.desc = d
+        self.dtype = dtype
+        self.handle = spfm_create_grid(d)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            spfm_destroy_grid(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # marshalling wrappers
+    def init_planar(self, c, lam, dx=1.0):
+        spfm_init_planar(self.handle, c, lam, dx)
+
+    def init_sphere(self, ctr, R, lam, dx=1.0):
+        spfm_init_sphere(self.handle, ctr, R, lam, dx)
+
+    def step(self, n_steps, M=1.0, Gamma=1.0, lam=4.0, dx=1.0, dt=0.1, dF=0.0, stencil=26,
+             scheme=SPFM_TI_GLOBAL):
+        spfm_step(self.handle, n_steps, M, Gamma, lam, dx, dt, dF, stencil, scheme)
+
+    def stats(self, flags=0, allow_nonfinite=False) -> dict:
+        return spfm_interface_stats(self.handle, flags, allow_nonfinite)
+
+    def current(self) -> torch.Tensor:
+        """View (nz, ny, nx) of the device buffer holding the current field."""
+        return self.fields[spfm_current(self.handle)][..., : self.shape[2]]
+
+    def get_field(self, to_host=True) -> torch.Tensor:
+        """Dense copy of the current field through spfm_get_field."""
+        tdt = TORCH_DTYPE[self.dtype]
+        if to_host:
+            out = torch.empty(self.shape, dtype=tdt, pin_memory=True)
+        else:
+            out = torch.empty(self.shape, dtype=tdt, device=self.fields[0].device)
+        spfm_get_field(self.handle, out.data_ptr(), 1 if to_host else 0)
+        return out
+
+    def set_field(self, src: torch.Tensor):
+        src = src.contiguous()
+        assert tuple(src.shape) == self.shape and src.dtype == TORCH_DTYPE[self.dtype]
+        spfm_set_field(self.handle, src.data_ptr(), 0 if src.is_cuda else 1)

@@ -1,0 +1,224 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64 oracle.
+
+Bars: FP64 max |phi_gpu - phi_oracle| <= 1e-12, FP32 <= 2e-5, interface velocity
+within 1e-4 relative.  Sizes span several tiles with ragged tails; the
+full-size cases compare sampled cells against oracle runs on their dependency
+cones.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1910_05180_gb300 import spfm as S
+from paper_1910_05180_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+TOL = {S.SPFM_F64: 1e-12, S.SPFM_F32: 2e-5}
+SCHEME_O = {S.SPFM_TI_GLOBAL: O.TI_GLOBAL, S.SPFM_FD: O.CF, S.SPFM_TI_LOCAL: O.TI_LOCAL}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    S.load()
+
+
+def make_pair(nx, ny, nz, dtype, bc, n, lam, dx=1.0, M=1.0, Gamma=1.0, dt=0.05, dF=0.0,
+              stencil=26, scheme=S.SPFM_TI_GLOBAL, gamma=(0, 0, 0), C_gamma=0.0):
+    g = S.Grid(nx, ny, nz, dtype=dtype, bc=bc, n=n, gamma=gamma, C_gamma=C_gamma)
+    p = O.Params(nx, ny, nz, bc=bc, n=tuple(n), lam=lam, dx=dx, M=M, Gamma=Gamma, dt=dt, dF=dF,
+                 stencil=stencil, scheme=SCHEME_O[scheme], gamma=gamma, C_gamma=C_gamma)
+    return g, p
+
+
+def upload(g, phi64, dtype):
+    t = torch.from_numpy(phi64).to(S.TORCH_DTYPE[dtype])
+    g.set_field(t.cuda())
+    return t.double().numpy()     # the values the GPU actually starts from
+
+
+def gpu_field(g):
+    return g.get_field(to_host=True).double().numpy()
+
+
+def rng_normal(seed):
+    return WL.random_normal(np.random.default_rng(seed))
+
+
+# ------------------------------------------------------------------ init
+
+
+@pytest.mark.parametrize("dtype", [S.SPFM_F64, S.SPFM_F32])
+def test_init_planar_and_sphere(dtype):
+    n = rng_normal(1)
+    g, p = make_pair(45, 23, 9, dtype, (S.SPFM_CONTACT,) * 6, n, lam=2.5, dx=0.7)
+    g.init_planar(7.1, 2.5, 0.7)
+    ref = O.init_planar(p, 7.1)
+    tol = 2e-16 if dtype == S.SPFM_F64 else 6e-8
+    assert np.abs(gpu_field(g) - ref).max() <= tol
+    ctr = (14.2, 8.1, 3.3)
+    g.init_sphere(ctr, 6.0, 2.5, 0.7)
+    ref = O.init_sphere(p, ctr, 6.0)
+    assert np.abs(gpu_field(g) - ref).max() <= tol
+
+
+# ------------------------------------------------------------ step parity
+
+CASES = [
+    # (shape, bc, stencil, scheme)
+    ((37, 21, 19), (S.SPFM_CONTACT,) * 6, 26, S.SPFM_TI_GLOBAL),
+    ((37, 21, 19), (S.SPFM_CONTACT,) * 6, 18, S.SPFM_TI_GLOBAL),
+    ((37, 21, 19), (S.SPFM_CONTACT,) * 6, 6, S.SPFM_TI_GLOBAL),
+    ((70, 18, 35), (S.SPFM_PERIODIC,) * 6, 26, S.SPFM_TI_GLOBAL),
+    ((67, 33, 17), (S.SPFM_NOFLUX, S.SPFM_NOFLUX, S.SPFM_PERIODIC, S.SPFM_PERIODIC,
+                    S.SPFM_CONTACT, S.SPFM_CONTACT), 26, S.SPFM_FD),
+    ((37, 21, 19), (S.SPFM_CONTACT,) * 6, 6, S.SPFM_FD),
+    ((5, 3, 2), (S.SPFM_CONTACT,) * 6, 26, S.SPFM_TI_GLOBAL),
+    ((1, 1, 40), (S.SPFM_PERIODIC,) * 4 + (S.SPFM_NOFLUX,) * 2, 26, S.SPFM_TI_GLOBAL),
+]
+
+
+@pytest.mark.parametrize("dtype", [S.SPFM_F64, S.SPFM_F32])
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_step_parity_small(dtype, case):
+    shape, bc, stencil, scheme = CASES[case]
+    nx, ny, nz = shape
+    n = rng_normal(10 + case)
+    if nx == 1 and ny == 1:
+        n = np.array([0.0, 0.0, 1.0])
+    lam = 2.0 + 0.5 * (case % 3)
+    g, p = make_pair(nx, ny, nz, dtype, bc, n, lam=lam, dt=0.05, dF=0.03, stencil=stencil,
+                     scheme=scheme)
+    rng = np.random.default_rng(100 + case)
+    c = float(n @ (np.array(shape) - 1) / 2.0)
+    phi0 = O.init_planar(p, c) + 0.01 * rng.random(p.shape)   # not an exact solution
+    start = upload(g, phi0, dtype)
+    steps = 40
+    g.step(steps, M=1.0, Gamma=1.0, lam=lam, dx=1.0, dt=0.05, dF=0.03, stencil=stencil,
+           scheme=scheme)
+    ref = O.step(p, start, steps)
+    err = np.abs(gpu_field(g) - ref).max()
+    assert err <= TOL[dtype], err
+
+
+def test_step_count_and_ping_pong_agree():
+    """n single steps and one n-step call give identical fields."""
+    n = rng_normal(3)
+    g1, _ = make_pair(40, 20, 12, S.SPFM_F32, (S.SPFM_CONTACT,) * 6, n, lam=3.0)
+    g2, _ = make_pair(40, 20, 12, S.SPFM_F32, (S.SPFM_CONTACT,) * 6, n, lam=3.0)
+    for g in (g1, g2):
+        g.init_planar(float(n @ [20, 10, 6]), 3.0)
+    g1.step(7, lam=3.0, dt=0.05, dF=0.02)
+    for _ in range(7):
+        g2.step(1, lam=3.0, dt=0.05, dF=0.02)
+    assert torch.equal(g1.get_field(), g2.get_field())
+
+
+# ---------------------------------------------------------------- stats
+
+
+@pytest.mark.parametrize("dtype", [S.SPFM_F64, S.SPFM_F32])
+def test_stats_and_energy_match_oracle(dtype):
+    n = rng_normal(7)
+    g, p = make_pair(50, 40, 30, dtype, (S.SPFM_CONTACT,) * 6, n, lam=2.0, stencil=26)
+    rng = np.random.default_rng(8)
+    phi0 = O.init_planar(p, float(n @ [25, 20, 15])) * (1 + 0.01 * rng.random(p.shape))
+    start = upload(g, phi0, dtype)
+    g.step(0, lam=2.0, dt=0.05)                       # sets the stats model
+    st = g.stats(S.SPFM_STATS_ENERGY)
+    ref = O.stats(p, start, (0.0, 0.0, 0.0))
+    for k in ("volume", "S_w", "S_c", "phi_min", "phi_max", "position"):
+        assert abs(st[k] - ref[k]) <= 1e-12 * max(1.0, abs(ref[k])), (k, st[k], ref[k])
+    e_ref = O.energy(p, start)
+    assert abs(st["energy"] - e_ref) <= 1e-12 * abs(e_ref)
+    # radius estimator on a sphere
+    ctr = (24.5, 19.5, 14.5)
+    g.init_sphere(ctr, 9.0, 2.0)
+    st = g.stats()
+    ref = O.stats(p, O.init_sphere(p, ctr, 9.0), ctr)
+    assert abs(st["radius"] - ref["radius"]) <= (1e-12 if dtype == S.SPFM_F64 else 1e-6)
+
+
+# --------------------------------------------------------------- config 1
+
+
+@pytest.mark.parametrize("scheme", [S.SPFM_TI_GLOBAL, S.SPFM_FD])
+def test_planar_100_fp64_1000_steps(scheme):
+    """Planar (1,0,0) interface, 128x32x32 FP64, 7-point, 1000 steps: field
+    parity <= 1e-12 and interface velocity against the oracle's (1e-4) and,
+    for SPFM, against v_th = -M dF/Gamma (1e-4)."""
+    w = WL.planar_100_128x32x32()
+    bc = WL.bc_codes(w)
+    g, p = make_pair(w["nx"], w["ny"], w["nz"], S.SPFM_F64, bc, w["n"], lam=w["lam"], dt=w["dt"],
+                     dF=w["dF"], stencil=w["stencil"], scheme=scheme)
+    g.init_planar(w["c"], w["lam"], w["dx"])
+    phi = O.init_planar(p, w["c"])
+    half = w["steps"] // 2
+    args = dict(M=1.0, Gamma=1.0, lam=w["lam"], dx=1.0, dt=w["dt"], dF=w["dF"], stencil=6, scheme=scheme)
+    g.step(half, **args)
+    c1 = g.stats()["position"]
+    phi = O.step(p, phi, half)
+    c1o = O.stats(p, phi)["position"]
+    g.step(w["steps"] - half, **args)
+    c2 = g.stats()["position"]
+    phi = O.step(p, phi, w["steps"] - half)
+    c2o = O.stats(p, phi)["position"]
+    assert np.abs(gpu_field(g) - phi).max() <= 1e-12
+    T = (w["steps"] - half) * w["dt"]
+    v, vo = (c2 - c1) / T, (c2o - c1o) / T
+    assert abs(v / vo - 1) < 1e-4
+    if scheme == S.SPFM_TI_GLOBAL:
+        assert abs(v / (-w["dF"]) - 1) < 1e-4
+
+
+# ----------------------------------------------------- full-size sampled
+
+
+def cone_reference(phi_start, shape, bc, sample, T, p_kwargs):
+    """Value of one cell after T steps, from an oracle run on the sub-box that
+    holds its dependency cone (cut faces T cells away from the sample)."""
+    nz, ny, nx = shape
+    idx = []
+    sub_bc = []
+    for ax, (c, N) in enumerate(zip(sample[::-1], (nx, ny, nz))):
+        lo, hi = max(0, c - T), min(N - 1, c + T)
+        idx.append((lo, hi))
+        sub_bc.append(bc[2 * ax] if lo == 0 else O.NOFLUX)
+        sub_bc.append(bc[2 * ax + 1] if hi == N - 1 else O.NOFLUX)
+    (x0, x1), (y0, y1), (z0, z1) = idx
+    sub = np.ascontiguousarray(phi_start[z0:z1 + 1, y0:y1 + 1, x0:x1 + 1])
+    p = O.Params(x1 - x0 + 1, y1 - y0 + 1, z1 - z0 + 1, bc=tuple(sub_bc), **p_kwargs)
+    # the contact BC and estimator use absolute positions only through n and
+    # differences, so a sub-box needs no origin shift
+    out = O.step(p, sub, T)
+    k, j, i = sample
+    return out[k - z0, j - y0, i - x0]
+
+
+@pytest.mark.parametrize("dtype", [S.SPFM_F32, S.SPFM_F64])
+def test_tilted_256cubed_sampled_cone_parity(dtype):
+    """256^3, normal (1,1,1)/sqrt3, 27-point SPFM, contact BCs on all faces, in
+    the launch configuration of the benchmark: 4 steps, 64 sampled cells
+    (corners, edges, faces, interior, interface) against dependency-cone oracle
+    runs."""
+    w = WL.tilted_111_256cubed()[0]
+    N, T = w["nx"], 4
+    bc = WL.bc_codes(w)
+    g = S.Grid(N, N, N, dtype=dtype, bc=bc, n=w["n"])
+    p = O.Params(N, N, N, bc=bc, n=w["n"], lam=w["lam"])
+    phi0 = O.init_planar(p, w["c"])
+    start = upload(g, phi0, dtype)
+    g.step(T, lam=w["lam"], dt=w["dt"], dF=w["dF"], stencil=26)
+    out = g.current().double().cpu().numpy()
+    rng = np.random.default_rng(5)
+    pts = [(z, y, x) for z in (0, N - 1) for y in (0, N - 1) for x in (0, N - 1)]
+    pts += [tuple(int(v) for v in rng.integers(0, N, 3)) for _ in range(24)]
+    pts += [(int(v), int(v), int(v)) for v in rng.integers(100, 156, 16)]   # across the interface
+    pts += [(0, int(a), int(b)) for a, b in rng.integers(0, N, (8, 2))]
+    pts += [(int(a), N - 1, int(b)) for a, b in rng.integers(0, N, (8, 2))]
+    kw = dict(n=w["n"], lam=w["lam"], dt=w["dt"], dF=w["dF"], stencil=26, scheme=O.TI_GLOBAL)
+    errs = [abs(out[s] - cone_reference(start, (N, N, N), bc, s, T, kw)) for s in pts]
+    assert max(errs) <= TOL[dtype], max(errs)
