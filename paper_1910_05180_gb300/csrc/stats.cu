@@ -37,37 +37,36 @@ template <> __device__ __forceinline__ __nv_bfloat16 wr<__nv_bfloat16>(double v)
 template <class S>
 __global__ void init_kernel(const InitArgs a, S *f)
 {
-    const long long total = a.g.plane * a.g.nz;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(idx % a.g.pitch);
-        const long long row = idx / a.g.pitch;
+    const long long rows = (long long)a.g.ny * a.g.nz;
+    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
         const int j = (int)(row % a.g.ny);
         const int k = (int)(row / a.g.ny);
-        double v = 0.0;
-        if (i < a.g.nx) {
-            const double px = a.dx * i, py = a.dx * j, pz = a.dx * k;
-            if (a.sphere) {
-                const double rx = px - a.ctr[0], ry = py - a.ctr[1], rz = pz - a.ctr[2];
-                const double r = sqrt(rx * rx + ry * ry + rz * rz);
-                v = 0.5 * (1.0 - tanh(2.0 * (a.R - r) / a.lambda));
-            } else {
-                const double pn = px * a.n[0] + py * a.n[1] + pz * a.n[2];
-                v = 0.5 * (1.0 - tanh(2.0 * (pn - a.c) / a.lambda));
+        S *r = f + (long long)k * a.g.plane + (long long)j * a.g.pitch;
+        for (int i = threadIdx.x; i < a.g.pitch; i += blockDim.x) {
+            double v = 0.0;
+            if (i < a.g.nx) {
+                const double px = a.dx * i, py = a.dx * j, pz = a.dx * k;
+                if (a.sphere) {
+                    const double rx = px - a.ctr[0], ry = py - a.ctr[1], rz = pz - a.ctr[2];
+                    const double rr = sqrt(rx * rx + ry * ry + rz * rz);
+                    v = 0.5 * (1.0 - tanh(2.0 * (a.R - rr) / a.lambda));
+                } else {
+                    const double pn = px * a.n[0] + py * a.n[1] + pz * a.n[2];
+                    v = 0.5 * (1.0 - tanh(2.0 * (pn - a.c) / a.lambda));
+                }
             }
+            r[i] = wr<S>(v);
         }
-        f[idx] = wr<S>(v);
     }
 }
 
 cudaError_t launch_init(const InitArgs &a, void *field, cudaStream_t st)
 {
-    const long long total = a.g.plane * a.g.nz;
-    long long blocks = (total + 255) / 256;
-    if (blocks > 4096) blocks = 4096;
-    if (a.dtype == SPFM_F64) init_kernel<double><<<(int)blocks, 256, 0, st>>>(a, (double *)field);
-    else if (a.dtype == SPFM_F32) init_kernel<float><<<(int)blocks, 256, 0, st>>>(a, (float *)field);
-    else init_kernel<__nv_bfloat16><<<(int)blocks, 256, 0, st>>>(a, (__nv_bfloat16 *)field);
+    const long long rows = (long long)a.g.ny * a.g.nz;
+    const int blocks = (int)(rows < 8192 ? rows : 8192);
+    if (a.dtype == SPFM_F64) init_kernel<double><<<blocks, 128, 0, st>>>(a, (double *)field);
+    else if (a.dtype == SPFM_F32) init_kernel<float><<<blocks, 128, 0, st>>>(a, (float *)field);
+    else init_kernel<__nv_bfloat16><<<blocks, 128, 0, st>>>(a, (__nv_bfloat16 *)field);
     return cudaGetLastError();
 }
 
@@ -135,41 +134,42 @@ __global__ void __launch_bounds__(256) stats_kernel(const StatsArgs a, const S *
     for (int i = 0; i < kNStat; ++i) v[i] = 0.0;
     v[4] = INFINITY;
     v[5] = -INFINITY;
-    const long long cells = (long long)a.g.nx * a.g.ny * a.g.nz;
     const double e_pref = a.Gamma / (a.C_gamma * a.lambda);
     const int nd = a.stencil == 6 ? 3 : (a.stencil == 18 ? 9 : 13);
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < cells;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(idx % a.g.nx);
-        const long long r = idx / a.g.nx;
-        const int j = (int)(r % a.g.ny);
-        const int k = (int)(r / a.g.ny);
-        const double ph = rd<S>(f, (long long)k * a.g.plane + (long long)j * a.g.pitch + i);
-        if (!isfinite(ph)) { v[6] += 1.0; continue; }
-        v[0] += ph;
-        v[4] = fmin(v[4], ph);
-        v[5] = fmax(v[5], ph);
-        if (ph > 1e-6 && ph < 1.0 - 1e-6) {
-            const double q = ph * (1.0 - ph);
-            const double psi = 0.5 * a.lambda * atanh(1.0 - 2.0 * ph);
-            const double px = a.dx * i, py = a.dx * j, pz = a.dx * k;
-            const double pn = px * a.n[0] + py * a.n[1] + pz * a.n[2];
-            const double rx = px - a.ctr[0], ry = py - a.ctr[1], rz = pz - a.ctr[2];
-            v[1] += q;
-            v[2] += q * (pn - psi);
-            v[3] += q * (sqrt(rx * rx + ry * ry + rz * rz) + psi);
-        }
-        if (a.energy) {
-            double e = 0.0;
-            for (int kk = 0; kk < nd; ++kk) {
-                const Dir d = grid_dir(kk);
-                const double r2 = (double)d.shell * a.dx * a.dx;
-                const double nb = ghost_value<S>(a, f, i + d.x, j + d.y, k + d.z);
-                const double dp = nb - ph;
-                e += a.w[kk] * (0.5 * a.lambda * a.lambda * dp * dp / r2 +
-                                potential(ph, a.a[kk], a.lambda * a.lambda / r2, a.scheme == SPFM_FD));
+    // rows in a fixed grid-stride order, cells of a row across the threads
+    const long long rows = (long long)a.g.ny * a.g.nz;
+    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int j = (int)(row % a.g.ny);
+        const int k = (int)(row / a.g.ny);
+        const S *fr = f + (long long)k * a.g.plane + (long long)j * a.g.pitch;
+        for (int i = threadIdx.x; i < a.g.nx; i += blockDim.x) {
+            const double ph = rd<S>(fr, i);
+            if (!isfinite(ph)) { v[6] += 1.0; continue; }
+            v[0] += ph;
+            v[4] = fmin(v[4], ph);
+            v[5] = fmax(v[5], ph);
+            if (ph > 1e-6 && ph < 1.0 - 1e-6) {
+                const double q = ph * (1.0 - ph);
+                const double psi = 0.5 * a.lambda * atanh(1.0 - 2.0 * ph);
+                const double px = a.dx * i, py = a.dx * j, pz = a.dx * k;
+                const double pn = px * a.n[0] + py * a.n[1] + pz * a.n[2];
+                const double rx = px - a.ctr[0], ry = py - a.ctr[1], rz = pz - a.ctr[2];
+                v[1] += q;
+                v[2] += q * (pn - psi);
+                v[3] += q * (sqrt(rx * rx + ry * ry + rz * rz) + psi);
             }
-            v[7] += e_pref * e;
+            if (a.energy) {
+                double e = 0.0;
+                for (int kk = 0; kk < nd; ++kk) {
+                    const Dir d = grid_dir(kk);
+                    const double r2 = (double)d.shell * a.dx * a.dx;
+                    const double nb = ghost_value<S>(a, f, i + d.x, j + d.y, k + d.z);
+                    const double dp = nb - ph;
+                    e += a.w[kk] * (0.5 * a.lambda * a.lambda * dp * dp / r2 +
+                                    potential(ph, a.a[kk], a.lambda * a.lambda / r2, a.scheme == SPFM_FD));
+                }
+                v[7] += e_pref * e;
+            }
         }
     }
     block_reduce_store(v, partials + (long long)blockIdx.x * kNStat);

@@ -1,23 +1,32 @@
 // step_kernel.cuh -- z-marching 2.5D stencil kernel of one explicit SPFM / CF step.
 //
-// One CTA owns an xy tile of TX*VX by TY cells and marches through a chunk of z
-// planes.  Each arriving plane is staged (with a one-cell halo whose ghost cells
-// come from the boundary conditions) in shared memory, double-buffered so one
-// __syncthreads per plane suffices; the next plane's 16-byte global loads are
-// issued before the barrier and land in registers while this plane is used.
+// One CTA owns an xy tile of TX*VX by TY cells (VX = cells per 16 bytes) and
+// marches through a chunk of z planes.  Each arriving plane is staged, with a
+// one-cell halo whose ghost cells come from the boundary conditions, in a
+// double-buffered shared-memory tile, so one __syncthreads per plane suffices;
+// the next plane's 16-byte global loads are issued before the barrier and land
+// in registers while this plane is being used.  The x/y ghost mapping of every
+// load slot is resolved once per CTA; per plane only the z mapping changes.
 //
 // From each plane every thread forms, for its cells, three plane quantities:
 //   C  = phi at the cell,
 //   F' = sum of the 4 in-plane face neighbours minus C (each as a difference),
 //   E' = sum of the 4 in-plane diagonal neighbours minus C,
-// kept in registers for the planes z-1, z, z+1.  The shell sums of the 27-point
-// stencil then follow without re-reading neighbours:
+// kept in registers for the planes z-1, z, z+1 (the z loop is unrolled by
+// three with rotating register roles, so nothing is copied between planes).
+// The shell sums of the 27-point stencil then follow without re-reading:
 //   S1 - 6 phi  = F'_z + t,             t = (C_{z-1} - phi) + (C_{z+1} - phi)
 //   S2 - 12 phi = E'_z + F'_{z-1} + F'_{z+1} + 4 t
 //   S3 - 8 phi  = E'_{z-1} + E'_{z+1} + 4 t
 // Every term is a difference of neighbouring values, which keeps FP32 drift far
-// below a plain sum of neighbours.  FP32 arithmetic runs on packed f32x2 pairs
-// (FFMA2/FADD2/FMUL2 of sm_100+); FP64 on scalar doubles.
+// below a plain sum of neighbours.
+//
+// FP32 arithmetic runs on packed f32x2 pairs (FFMA2/FADD2/FMUL2 of sm_100+).  A
+// thread's four cells x..x+3 form the packs A = (x, x+2) and B = (x+1, x+3);
+// shared memory holds every 16-byte quad in the order (v0, v2, v1, v3), so one
+// 128-bit shared load yields both packs in aligned register pairs and the
+// x-neighbour packs are W(A) = (x-1, x+1), E(A) = B, W(B) = A, E(B) = (x+2, x+4).
+// FP64 runs on scalar doubles with the same structure.
 #pragma once
 
 #include "spfm_internal.h"
@@ -31,7 +40,6 @@ template <class T> struct Pk;
 template <> struct Pk<float> {
     using P = float2;
     static __device__ __forceinline__ P mk(float a, float b) { return make_float2(a, b); }
-    static __device__ __forceinline__ P splat(float a) { return make_float2(a, a); }
     static __device__ __forceinline__ P add(P a, P b) { return __fadd2_rn(a, b); }
     static __device__ __forceinline__ P mul(P a, P b) { return __fmul2_rn(a, b); }
     static __device__ __forceinline__ P fma(P a, P b, P c) { return __ffma2_rn(a, b, c); }
@@ -42,10 +50,11 @@ template <> struct Pk<float> {
     }
 };
 
+struct D2 { double x, y; };
+
 template <> struct Pk<double> {
-    struct P { double x, y; };
+    using P = D2;
     static __device__ __forceinline__ P mk(double a, double b) { return {a, b}; }
-    static __device__ __forceinline__ P splat(double a) { return {a, a}; }
     static __device__ __forceinline__ P add(P a, P b) { return {a.x + b.x, a.y + b.y}; }
     static __device__ __forceinline__ P mul(P a, P b) { return {a.x * b.x, a.y * b.y}; }
     static __device__ __forceinline__ P fma(P a, P b, P c)
@@ -55,6 +64,41 @@ template <> struct Pk<double> {
     static __device__ __forceinline__ P sub(P a, P b) { return {a.x - b.x, a.y - b.y}; }
     static __device__ __forceinline__ P div(P a, P b) { return {a.x / b.x, a.y / b.y}; }
 };
+
+template <class T> struct PackT;
+template <> struct PackT<float> { using P = float2; static P splat(float v) { return make_float2(v, v); } };
+template <> struct PackT<double> { using P = D2; static P splat(double v) { return {v, v}; } };
+
+// Step coefficients pre-splatted into packs (kernel parameter space).
+template <class T>
+struct PackCoef {
+    using P = typename PackT<T>::P;
+    P one, m2, four, c1, c2, c3, dt, nkmu, kappa;
+    P nA[kMaxTerms], beta[kMaxTerms];
+    int nterms;
+};
+
+template <class T>
+inline PackCoef<T> make_pack_coef(const StepCoef<T> &c)
+{
+    using PT = PackT<T>;
+    PackCoef<T> p;
+    p.one = PT::splat(T(1));
+    p.m2 = PT::splat(T(-2));
+    p.four = PT::splat(T(4));
+    p.c1 = PT::splat(c.c1);
+    p.c2 = PT::splat(c.c2);
+    p.c3 = PT::splat(c.c3);
+    p.dt = PT::splat(c.dt);
+    p.nkmu = PT::splat(-c.kmu);
+    p.kappa = PT::splat(c.kappa);
+    for (int k = 0; k < kMaxTerms; ++k) {
+        p.nA[k] = PT::splat(-c.A[k]);
+        p.beta[k] = PT::splat(c.beta[k]);
+    }
+    p.nterms = c.nterms;
+    return p;
+}
 
 // ------------------------------------------------------ storage <-> compute
 
@@ -116,41 +160,144 @@ template <> struct Io<__nv_bfloat16, float> {
     static __device__ __forceinline__ __nv_bfloat16 cvt_out(float t) { return __float2bfloat16_rn(t); }
 };
 
-// Element (gx, gy, gz) of the source with ghost cells from the boundary
-// conditions; up to one cell outside per axis, 0 beyond (never used as data).
-template <class S, class T>
-__device__ __forceinline__ T load_elem(const StepCoef<T> &C, const S *__restrict__ src, int gx,
-                                       int gy, int gz)
+// ------------------------------------------------------------- load slots
+
+// One staged load of a plane: a row of VX cells (or one cell) whose x/y ghost
+// mapping is fixed for the whole z march.
+struct Slot {
+    long long row;   // sy * pitch (+ gx when xfull)
+    int gx;          // first x of the slot
+    int yface;       // contact face of the y mapping, or -1
+    int mode;        // 0 inactive (value unused), 1 full vector in range, 2 per element
+};
+
+__device__ __forceinline__ Slot make_slot(const GridGeom &g, int gx, int gy, int width)
 {
-    const GridGeom &g = C.g;
-    if (gx < -1 || gx > g.nx || gy < -1 || gy > g.ny || gz < -1 || gz > g.nz) return T(0);
-    int fx, fy, fz;
-    const int sx = map_axis(gx, g.nx, g.bc[0], g.bc[1], &fx, 0);
-    const int sy = map_axis(gy, g.ny, g.bc[2], g.bc[3], &fy, 2);
-    const int sz = map_axis(gz, g.nz, g.bc[4], g.bc[5], &fz, 4);
-    T v = Io<S, T>::cvt_in(src[(long long)sz * g.plane + (long long)sy * g.pitch + sx]);
-    // contact shifts compose (they are translations of the ideal profile)
-    if (fx >= 0) v = contact_shift<T>(v, C.aface[fx]);
-    if (fy >= 0) v = contact_shift<T>(v, C.aface[fy]);
-    if (fz >= 0) v = contact_shift<T>(v, C.aface[fz]);
-    return v;
+    Slot s;
+    s.gx = gx;
+    s.yface = -1;
+    if (gy < -1 || gy > g.ny || gx > g.nx || gx + width - 1 < -1) {
+        s.mode = 0;
+        s.row = 0;
+        return s;
+    }
+    const int sy = map_axis(gy, g.ny, g.bc[2], g.bc[3], &s.yface, 2);
+    s.row = (long long)sy * g.pitch;
+    if (gx >= 0 && gx + width <= g.nx) {
+        s.mode = 1;
+        s.row += gx;
+    } else {
+        s.mode = 2;
+    }
+    return s;
 }
 
-template <class S, class T>
-__device__ __forceinline__ void fetch_vec(const StepCoef<T> &C, const S *__restrict__ src, int gx,
-                                          int gy, int gz, T *out)
+// Loads the slot's `width` cells of plane (already z-mapped) `pbase`, applying
+// the ghost maps of x (per element), y (per slot) and z (per plane).
+template <class S, class T, int WIDTH>
+__device__ __forceinline__ void load_slot(const StepCoef<T> &C, const S *__restrict__ pbase,
+                                          const Slot &s, int zface, T *out)
 {
-    constexpr int VX = Io<S, T>::VX;
-    const GridGeom &g = C.g;
-    if (gz >= 0 && gz < g.nz && gy >= 0 && gy < g.ny && gx >= 0 && gx + VX <= g.nx) {
-        Io<S, T>::ld(src + (long long)gz * g.plane + (long long)gy * g.pitch + gx, out);
+    if (s.mode == 1) {
+        if (WIDTH == 1) out[0] = Io<S, T>::cvt_in(pbase[s.row]);
+        else Io<S, T>::ld(pbase + s.row, out);
+    } else if (s.mode == 2) {
+#pragma unroll
+        for (int e = 0; e < WIDTH; ++e) {
+            const int gx = s.gx + e;
+            T v = T(0);
+            if (gx >= -1 && gx <= C.g.nx) {
+                int fx;
+                const int sx = map_axis(gx, C.g.nx, C.g.bc[0], C.g.bc[1], &fx, 0);
+                v = Io<S, T>::cvt_in(pbase[s.row + sx]);
+                if (fx >= 0) v = contact_shift<T>(v, C.aface[fx]);
+            }
+            out[e] = v;
+        }
     } else {
 #pragma unroll
-        for (int e = 0; e < VX; ++e) out[e] = load_elem<S, T>(C, src, gx + e, gy, gz);
+        for (int e = 0; e < WIDTH; ++e) out[e] = T(0);
+    }
+    if (s.yface >= 0) {
+#pragma unroll
+        for (int e = 0; e < WIDTH; ++e) out[e] = contact_shift<T>(out[e], C.aface[s.yface]);
+    }
+    if (zface >= 0) {
+#pragma unroll
+        for (int e = 0; e < WIDTH; ++e) out[e] = contact_shift<T>(out[e], C.aface[zface]);
     }
 }
 
-// cells of pack p (two lanes): for VX = 2 (0,1); otherwise (0,2),(1,3),(4,6),(5,7)
+// ------------------------------------------------------ shared-memory rows
+
+// Shared rows hold quads of 4 cells in the order (v0, v2, v1, v3) for VX >= 4.
+template <class T, int VX>
+__device__ __forceinline__ void put_row(T *dst, const T *v)
+{
+    if constexpr (VX == 2) {
+        dst[0] = v[0];
+        dst[1] = v[1];
+    } else {
+#pragma unroll
+        for (int q = 0; q < VX / 4; ++q) {
+            if constexpr (sizeof(T) == 4) {
+                *reinterpret_cast<float4 *>(dst + 4 * q) =
+                    make_float4(v[4 * q], v[4 * q + 2], v[4 * q + 1], v[4 * q + 3]);
+            } else {
+                dst[4 * q] = v[4 * q];
+                dst[4 * q + 1] = v[4 * q + 2];
+                dst[4 * q + 2] = v[4 * q + 1];
+                dst[4 * q + 3] = v[4 * q + 3];
+            }
+        }
+    }
+}
+
+// The packs of one shared row around a thread's cells: C[p], W[p], E[p].
+template <class T, int VX>
+struct RowPacks {
+    using P = typename Pk<T>::P;
+    static constexpr int NP = VX / 2;
+    P c[NP], w[NP], e[NP];
+};
+
+template <class T, int VX>
+__device__ __forceinline__ void get_row(const T *r, RowPacks<T, VX> &o)
+{
+    using K = Pk<T>;
+    if constexpr (VX == 2) {
+        const T l = r[-1], v0 = r[0], v1 = r[1], rr = r[2];
+        o.c[0] = K::mk(v0, v1);
+        o.w[0] = K::mk(l, v0);
+        o.e[0] = K::mk(v1, rr);
+    } else {
+        constexpr int NQ = VX / 4;
+        typename Pk<T>::P a[NQ], b[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            if constexpr (sizeof(T) == 4) {
+                const float4 f = *reinterpret_cast<const float4 *>(r + 4 * q);
+                a[q] = K::mk(f.x, f.y);   // (v0, v2)
+                b[q] = K::mk(f.z, f.w);   // (v1, v3)
+            } else {
+                a[q] = K::mk(r[4 * q], r[4 * q + 1]);
+                b[q] = K::mk(r[4 * q + 2], r[4 * q + 3]);
+            }
+        }
+        const T l = r[-1], rr = r[VX];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            o.c[2 * q] = a[q];
+            o.c[2 * q + 1] = b[q];
+            o.w[2 * q] = K::mk(q == 0 ? l : b[q - 1].y, b[q].x);          // (x-1, x+1)
+            o.e[2 * q] = b[q];                                            // (x+1, x+3)
+            o.w[2 * q + 1] = a[q];                                        // (x,   x+2)
+            o.e[2 * q + 1] = K::mk(a[q].y, q == NQ - 1 ? rr : a[q + 1].x);  // (x+2, x+4)
+        }
+    }
+}
+
+// cell index (0..VX-1) of lane `lane` of pack p
 template <int VX>
 __device__ __forceinline__ constexpr int pack_cell(int p, int lane)
 {
@@ -169,11 +316,17 @@ struct TileShape {
     static constexpr int SMEM_ELEMS = 2 * ROWS * SW;
 };
 
+template <class T, int NP>
+struct PlaneQ {
+    using P = typename Pk<T>::P;
+    P c[NP], f[NP], e[NP];
+};
+
 // KIND: 0 = CF potential, 1 = TI global with <= 4 groups, 2 = TI global <= 13 groups
 template <class S, class T, int STENCIL, int KIND, int TX, int TY>
-__device__ __forceinline__ void step_tile(const StepCoef<T> &C, const S *__restrict__ src,
-                                          S *__restrict__ dst, int bx, int by, int zc0, int zc1,
-                                          T *__restrict__ sbuf)
+__device__ __forceinline__ void step_tile(const StepCoef<T> &C, const PackCoef<T> &PC,
+                                          const S *__restrict__ src, S *__restrict__ dst, int bx,
+                                          int by, int zc0, int zc1, T *__restrict__ sbuf)
 {
     using Sh = TileShape<S, T, TX, TY>;
     using K = Pk<T>;
@@ -188,130 +341,102 @@ __device__ __forceinline__ void step_tile(const StepCoef<T> &C, const S *__restr
     const int gy = y0 + ty;
     const bool has_extra = ty < 2;
     const int extra_row = ty == 0 ? 0 : ROWS - 1;
-    const int extra_gy = ty == 0 ? y0 - 1 : y0 + TY;
     const bool has_side = tid < 2 * ROWS;
     const int side_row = tid >> 1, side_right = tid & 1;
-    const int side_gx = side_right ? x0 + W : x0 - 1;
-    const int side_gy = y0 + side_row - 1;
     const bool out_ok = gy < g.ny && gx < g.nx;
 
-    T own[VX], extra[VX], side = T(0);
-#pragma unroll
-    for (int e = 0; e < VX; ++e) extra[e] = T(0);
+    // x/y ghost mapping of the three load slots, fixed for the whole march
+    const Slot s_own = make_slot(g, gx, gy, VX);
+    const Slot s_extra = has_extra ? make_slot(g, gx, ty == 0 ? y0 - 1 : y0 + TY, VX) : Slot{0, 0, -1, 0};
+    const Slot s_side = has_side ? make_slot(g, side_right ? x0 + W : x0 - 1, y0 + side_row - 1, 1)
+                                 : Slot{0, 0, -1, 0};
+    T *const own_dst0 = sbuf + (ty + 1) * SW + VX + tx * VX;
+    T *const extra_dst0 = sbuf + extra_row * SW + VX + tx * VX;
+    T *const side_dst0 = sbuf + side_row * SW + (side_right ? VX + W : VX - 1);
 
+    T own[VX], extra[VX], side[1];
     auto fetch = [&](int z) {
-        fetch_vec<S, T>(C, src, gx, gy, z, own);
-        if (has_extra) fetch_vec<S, T>(C, src, gx, extra_gy, z, extra);
-        if (has_side) side = load_elem<S, T>(C, src, side_gx, side_gy, z);
+        int zf;
+        const int sz = map_axis(z, g.nz, g.bc[4], g.bc[5], &zf, 4);
+        const S *pb = src + (long long)sz * g.plane;
+        load_slot<S, T, VX>(C, pb, s_own, zf, own);
+        if (has_extra) load_slot<S, T, VX>(C, pb, s_extra, zf, extra);
+        if (has_side) load_slot<S, T, 1>(C, pb, s_side, zf, side);
     };
 
-    P Cm[NP], Fm[NP], Em[NP], C0[NP], F0[NP], E0[NP];
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-        Cm[p] = C0[p] = Fm[p] = F0[p] = Em[p] = E0[p] = K::splat(T(0));
-    }
+    S *out_base = dst + (long long)gy * g.pitch + gx;
 
-    const P one = K::splat(T(1)), m2 = K::splat(T(-2)), four = K::splat(T(4));
-    const P pc1 = K::splat(C.c1), pc2 = K::splat(C.c2), pc3 = K::splat(C.c3);
-    const P pdt = K::splat(C.dt), pnkmu = K::splat(-C.kmu), pkap = K::splat(C.kappa);
-
-    fetch(zc0 - 1);
-    int it = 0;
-    for (int pz = zc0 - 1; pz <= zc1; ++pz, ++it) {
-        T *b = sbuf + (it & 1) * (ROWS * SW);
-        // publish the staged plane pz
-        {
-            T *row = b + (ty + 1) * SW + VX + tx * VX;
-#pragma unroll
-            for (int e = 0; e < VX; ++e) row[e] = own[e];
-            if (has_extra) {
-                T *er = b + extra_row * SW + VX + tx * VX;
-#pragma unroll
-                for (int e = 0; e < VX; ++e) er[e] = extra[e];
-            }
-            if (has_side) b[side_row * SW + (side_right ? VX + W : VX - 1)] = side;
-        }
+    // one arriving plane: publish, prefetch the next, reduce to plane quantities,
+    // and emit the output plane pz-1 from (m, z, p).  Returns false after the last.
+    auto body = [&](int k, PlaneQ<T, NP> &m, PlaneQ<T, NP> &z, PlaneQ<T, NP> &p) -> bool {
+        const int pz = zc0 - 1 + k;
+        const int boff = (k & 1) * (ROWS * SW);
+        put_row<T, VX>(own_dst0 + boff, own);
+        if (has_extra) put_row<T, VX>(extra_dst0 + boff, extra);
+        if (has_side) side_dst0[boff] = side[0];
         if (pz < zc1) fetch(pz + 1);
         __syncthreads();
 
-        // plane quantities of plane pz for this thread's cells
-        P Cp[NP], Fp[NP], Ep[NP];
         {
-            const T *r0 = b + (ty + 1) * SW + VX + tx * VX;
-            const T *rn = r0 - SW;
-            const T *rs = r0 + SW;
-            T v0[VX + 2], vn[VX + 2], vs[VX + 2];
+            const T *r0 = own_dst0 + boff;
+            RowPacks<T, VX> rc, rn, rs;
+            get_row<T, VX>(r0, rc);
+            get_row<T, VX>(r0 - SW, rn);
+            get_row<T, VX>(r0 + SW, rs);
 #pragma unroll
-            for (int e = -1; e <= VX; ++e) v0[e + 1] = r0[e];
-#pragma unroll
-            for (int e = 0; e < VX; ++e) { vn[e + 1] = rn[e]; vs[e + 1] = rs[e]; }
-            if (STENCIL != 6) {
-                vn[0] = rn[-1]; vn[VX + 1] = rn[VX];
-                vs[0] = rs[-1]; vs[VX + 1] = rs[VX];
-            }
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                const int i0 = pack_cell<VX>(p, 0) + 1, i1 = pack_cell<VX>(p, 1) + 1;
-                const P c = K::mk(v0[i0], v0[i1]);
-                const P w = K::mk(v0[i0 - 1], v0[i1 - 1]);
-                const P e = K::mk(v0[i0 + 1], v0[i1 + 1]);
-                const P n = K::mk(vn[i0], vn[i1]);
-                const P s = K::mk(vs[i0], vs[i1]);
-                Cp[p] = c;
-                Fp[p] = K::add(K::add(K::sub(w, c), K::sub(e, c)), K::add(K::sub(n, c), K::sub(s, c)));
-                if (STENCIL != 6) {
-                    const P nw = K::mk(vn[i0 - 1], vn[i1 - 1]), ne = K::mk(vn[i0 + 1], vn[i1 + 1]);
-                    const P sw = K::mk(vs[i0 - 1], vs[i1 - 1]), se = K::mk(vs[i0 + 1], vs[i1 + 1]);
-                    Ep[p] = K::add(K::add(K::sub(nw, c), K::sub(ne, c)), K::add(K::sub(sw, c), K::sub(se, c)));
-                } else {
-                    Ep[p] = K::splat(T(0));
-                }
+            for (int q = 0; q < NP; ++q) {
+                const P c = rc.c[q];
+                p.c[q] = c;
+                p.f[q] = K::add(K::add(K::sub(rc.w[q], c), K::sub(rc.e[q], c)),
+                                K::add(K::sub(rn.c[q], c), K::sub(rs.c[q], c)));
+                if (STENCIL != 6)
+                    p.e[q] = K::add(K::add(K::sub(rn.w[q], c), K::sub(rn.e[q], c)),
+                                    K::add(K::sub(rs.w[q], c), K::sub(rs.e[q], c)));
             }
         }
 
-        if (pz >= zc0 + 1 && out_ok) {
+        if (k >= 2 && out_ok) {
             T outv[VX];
 #pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                const P ph = C0[p];
-                const P t = K::add(K::sub(Cm[p], ph), K::sub(Cp[p], ph));
-                P lap = K::mul(pc1, K::add(F0[p], t));
+            for (int q = 0; q < NP; ++q) {
+                const P ph = z.c[q];
+                const P t = K::add(K::sub(m.c[q], ph), K::sub(p.c[q], ph));
+                P lap = K::mul(PC.c1, K::add(z.f[q], t));
                 if (STENCIL != 6) {
-                    const P s2 = K::fma(four, t, K::add(E0[p], K::add(Fm[p], Fp[p])));
-                    lap = K::fma(pc2, s2, lap);
+                    const P s2 = K::fma(PC.four, t, K::add(z.e[q], K::add(m.f[q], p.f[q])));
+                    lap = K::fma(PC.c2, s2, lap);
                 }
                 if (STENCIL == 26) {
-                    const P s3 = K::fma(four, t, K::add(Em[p], Ep[p]));
-                    lap = K::fma(pc3, s3, lap);
+                    const P s3 = K::fma(PC.four, t, K::add(m.e[q], p.e[q]));
+                    lap = K::fma(PC.c3, s3, lap);
                 }
-                const P s = K::fma(m2, ph, one);              // 1 - 2 phi
-                const P q = K::mul(ph, K::sub(one, ph));       // phi (1 - phi)
-                const P qs = K::mul(q, s);
+                const P s = K::fma(PC.m2, ph, PC.one);          // 1 - 2 phi
+                const P q1 = K::mul(ph, K::sub(PC.one, ph));     // phi (1 - phi)
+                const P qs = K::mul(q1, s);
                 P pot;
                 if (KIND == 0) {
-                    pot = K::mul(pkap, qs);
+                    pot = K::mul(PC.kappa, qs);
                 } else {
                     const P u = K::mul(s, s);
-                    P num = K::splat(C.beta[0]);
-                    P den = K::fma(K::splat(-C.A[0]), u, one);
+                    P num = PC.beta[0];
+                    P den = K::fma(PC.nA[0], u, PC.one);
 #pragma unroll
-                    for (int k = 1; k < NTMAX; ++k) {
-                        if (k < C.nterms) {
-                            const P d = K::fma(K::splat(-C.A[k]), u, one);
-                            num = K::fma(num, d, K::mul(K::splat(C.beta[k]), den));
+                    for (int kk = 1; kk < NTMAX; ++kk) {
+                        if (kk < PC.nterms) {
+                            const P d = K::fma(PC.nA[kk], u, PC.one);
+                            num = K::fma(num, d, K::mul(PC.beta[kk], den));
                             den = K::mul(den, d);
                         }
                     }
                     pot = K::mul(qs, K::div(num, den));
                 }
                 P R = K::sub(lap, pot);
-                R = K::fma(pnkmu, q, R);
-                const P o = K::fma(pdt, R, ph);
-                outv[pack_cell<VX>(p, 0)] = o.x;
-                outv[pack_cell<VX>(p, 1)] = o.y;
+                R = K::fma(PC.nkmu, q1, R);
+                const P o = K::fma(PC.dt, R, ph);
+                outv[pack_cell<VX>(q, 0)] = o.x;
+                outv[pack_cell<VX>(q, 1)] = o.y;
             }
-            const int oz = pz - 1;
-            S *optr = dst + (long long)oz * g.plane + (long long)gy * g.pitch + gx;
+            S *optr = out_base + (long long)(pz - 1) * g.plane;
             if (gx + VX <= g.nx) {
                 Io<S, T>::st(optr, outv);
             } else {
@@ -320,23 +445,31 @@ __device__ __forceinline__ void step_tile(const StepCoef<T> &C, const S *__restr
                     if (gx + e < g.nx) optr[e] = Io<S, T>::cvt_out(outv[e]);
             }
         }
-#pragma unroll
-        for (int p = 0; p < NP; ++p) {
-            Cm[p] = C0[p]; Fm[p] = F0[p]; Em[p] = E0[p];
-            C0[p] = Cp[p]; F0[p] = Fp[p]; E0[p] = Ep[p];
-        }
+        return pz < zc1;
+    };
+
+    PlaneQ<T, NP> q0, q1, q2;
+    fetch(zc0 - 1);
+    for (int k = 0;; k += 3) {
+        if (!body(k, q1, q2, q0)) break;
+        if (!body(k + 1, q2, q0, q1)) break;
+        if (!body(k + 2, q0, q1, q2)) break;
     }
 }
 
+// minimum resident CTAs per SM: caps registers so three 256-thread CTAs fit
+template <class T> struct MinBlocks { static constexpr int value = sizeof(T) == 4 ? 3 : 2; };
+
 template <class S, class T, int STENCIL, int KIND, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY)
-    spfm_step_kernel(const StepCoef<T> C, const S *__restrict__ src, S *__restrict__ dst, int zchunk)
+__global__ void __launch_bounds__(TX *TY, MinBlocks<T>::value)
+    spfm_step_kernel(const StepCoef<T> C, const PackCoef<T> PC, const S *__restrict__ src,
+                     S *__restrict__ dst, int zchunk)
 {
     using Sh = TileShape<S, T, TX, TY>;
     __shared__ __align__(16) T sbuf[Sh::SMEM_ELEMS];
     const int zc0 = blockIdx.z * zchunk;
     const int zc1 = min(zc0 + zchunk, C.g.nz);
-    step_tile<S, T, STENCIL, KIND, TX, TY>(C, src, dst, blockIdx.x, blockIdx.y, zc0, zc1, sbuf);
+    step_tile<S, T, STENCIL, KIND, TX, TY>(C, PC, src, dst, blockIdx.x, blockIdx.y, zc0, zc1, sbuf);
 }
 
 // z-chunk length so that the launch has enough CTAs for 152 SMs
@@ -359,8 +492,9 @@ cudaError_t launch_step_t(const StepCoef<T> &c, const S *src, S *dst, LaunchCfg 
     const int zchunk = pick_zchunk(gxn * gyn, c.g.nz);
     const dim3 grid(gxn, gyn, (c.g.nz + zchunk - 1) / zchunk);
     const int kind = cfg.scheme == SPFM_FD ? 0 : (c.nterms <= 4 ? 1 : 2);
+    const PackCoef<T> pc = make_pack_coef<T>(c);
 #define SPFM_LAUNCH(ST, KD) \
-    spfm_step_kernel<S, T, ST, KD, TX, TY><<<grid, block, 0, st>>>(c, src, dst, zchunk)
+    spfm_step_kernel<S, T, ST, KD, TX, TY><<<grid, block, 0, st>>>(c, pc, src, dst, zchunk)
 #define SPFM_BY_KIND(ST)                        \
     do {                                        \
         if (kind == 0) SPFM_LAUNCH(ST, 0);      \

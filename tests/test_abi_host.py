@@ -1,0 +1,160 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point declared in include/*.h, computes layouts, and rejects bad
+arguments before any CUDA call (validation runs first in every entry point).
+"""
+import ctypes
+import glob
+import math
+import os
+import re
+
+import pytest
+
+from paper_1910_05180_gb300 import build as B
+from paper_1910_05180_gb300 import spfm as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return S.load()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(spfm_[a-z0-9_]+)\s*\(",
+                             text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    # and the binding marshals every one of them
+    bound = {s[0] for s in S.SIGNATURES}
+    assert set(names) <= bound, set(names) - bound
+
+
+def _desc(nx=10, ny=7, nz=5, dtype=S.SPFM_F32, bc=(S.SPFM_PERIODIC,) * 6, n=(1.0, 0.0, 0.0)):
+    d = S.GridDesc()
+    d.nx, d.ny, d.nz, d.dtype = nx, ny, nz, dtype
+    for i in range(6):
+        d.bc[i] = bc[i]
+    for i in range(3):
+        d.n[i] = n[i]
+    return d
+
+
+@pytest.mark.parametrize("dtype,per16", [(S.SPFM_F64, 2), (S.SPFM_F32, 4), (S.SPFM_BF16, 8)])
+def test_layout_pitch_is_16_byte_rows(lib, dtype, per16):
+    for nx in (1, 3, 4, 17, 128, 130):
+        px, fb, sb = S.spfm_layout(_desc(nx=nx, dtype=dtype))
+        assert px % per16 == 0 and nx <= px < nx + per16
+        es = {S.SPFM_F64: 8, S.SPFM_F32: 4, S.SPFM_BF16: 2}[dtype]
+        assert fb == px * 7 * 5 * es
+        assert sb > 0
+
+
+def _fake_grid(lib, **kw):
+    """A handle over fake, aligned pointers: fine for calls that fail validation."""
+    d = _desc(**kw)
+    _, _, sb = S.spfm_layout(d)
+    d.field[0], d.field[1] = 0x10000, 0x20000
+    d.scratch, d.scratch_bytes = 0x30000, sb
+    return S.spfm_create_grid(d)
+
+
+def test_create_grid_validation(lib):
+    d = _desc(nx=0)
+    with pytest.raises(S.SpfmError) as e:
+        S.spfm_create_grid(d)
+    assert e.value.status == S.SPFM_EINVAL
+    d = _desc(n=(1.0, 1.0, 0.0))
+    d.field[0], d.field[1], d.scratch, d.scratch_bytes = 0x10000, 0x20000, 0x30000, 1 << 20
+    with pytest.raises(S.SpfmError) as e:
+        S.spfm_create_grid(d)
+    assert "|n|" in str(e.value)
+    d = _desc(bc=(S.SPFM_PERIODIC, S.SPFM_NOFLUX) + (S.SPFM_PERIODIC,) * 4)
+    d.field[0], d.field[1], d.scratch, d.scratch_bytes = 0x10000, 0x20000, 0x30000, 1 << 20
+    with pytest.raises(S.SpfmError):
+        S.spfm_create_grid(d)
+    d = _desc()
+    d.field[0], d.field[1], d.scratch, d.scratch_bytes = 0x10008, 0x20000, 0x30000, 1 << 20
+    with pytest.raises(S.SpfmError):
+        S.spfm_create_grid(d)      # unaligned field
+    d = _desc()
+    d.field[0], d.field[1], d.scratch, d.scratch_bytes = 0x10000, 0x20000, 0x30000, 8
+    with pytest.raises(S.SpfmError) as e:
+        S.spfm_create_grid(d)
+    assert e.value.status == S.SPFM_ENOMEM
+
+
+def test_step_validation_before_any_launch(lib):
+    h = _fake_grid(lib)
+    try:
+        with pytest.raises(S.SpfmError) as e:
+            S.spfm_step(h, 1, 1.0, 1.0, 4.0, 1.0, 0.1, 0.0, 7, S.SPFM_TI_GLOBAL)
+        assert e.value.status == S.SPFM_EINVAL
+        with pytest.raises(S.SpfmError) as e:
+            S.spfm_step(h, 1, 1.0, 1.0, -4.0, 1.0, 0.1, 0.0, 26, S.SPFM_TI_GLOBAL)
+        assert e.value.status == S.SPFM_EINVAL
+        # 7-point, D = M = 1: Laplacian spectral radius 12 -> dt must stay below 1/6
+        with pytest.raises(S.SpfmError) as e:
+            S.spfm_step(h, 1, 1.0, 1.0, 4.0, 1.0, 0.2, 0.0, 6, S.SPFM_FD)
+        assert e.value.status == S.SPFM_EUNSTABLE
+    finally:
+        S.spfm_destroy_grid(h)
+
+
+def test_phase_stability_limit_of_cf(lib):
+    """Sec. 3.1: CF + h3 needs |dF dx/Gamma| < 8/(3 C_Gamma lambda/dx)."""
+    h = _fake_grid(lib)
+    try:
+        lam, Cg = 4.0, 2.0 / 3.0
+        limit = 8.0 / (3.0 * Cg * lam)
+        with pytest.raises(S.SpfmError) as e:
+            S.spfm_step(h, 0, 1.0, 1.0, lam, 1.0, 0.01, 1.001 * limit, 26, S.SPFM_FD)
+        assert e.value.status == S.SPFM_EPHASE
+        # just below the limit passes validation (0 steps: nothing is launched)
+        S.spfm_step(h, 0, 1.0, 1.0, lam, 1.0, 0.01, 0.999 * limit, 26, S.SPFM_FD)
+        # TI has no such limit in this form
+        S.spfm_step(h, 0, 1.0, 1.0, lam, 1.0, 0.01, 1.5 * limit, 26, S.SPFM_TI_GLOBAL)
+    finally:
+        S.spfm_destroy_grid(h)
+
+
+def test_euler_bound_matches_spectral_radius(lib):
+    """The EUNSTABLE bound uses the exact spectral radius of the Laplacian part
+    (6.67 D for the default 26-neighbour weights) plus the potential curvature."""
+    h = _fake_grid(lib, n=(1.0, 0.0, 0.0))
+    try:
+        lam = 40.0   # potential curvature small at large lambda
+        # D = 1: c1 = 1/2, c2 = 1/12, c3 = 1/24; bound = 20/3 + pot
+        pot = 0.0
+        w = [0.5] * 3 + [1.0 / 12] * 6 + [1.0 / 24] * 4     # c_k = D w_k / |r_k|^2
+        d = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (0, 1, 1), (1, 0, 1), (1, -1, 0), (0, 1, -1),
+             (1, 0, -1), (1, 1, 1), (-1, 1, 1), (1, -1, 1), (1, 1, -1)]
+        for k in range(13):
+            a = math.tanh(2.0 * d[k][0] / lam)
+            pot += 4 * w[k] * a * a / (1 - a * a)
+        bound = 20.0 / 3.0 + pot
+        S.spfm_step(h, 0, 1.0, 1.0, lam, 1.0, 0.999 * 2 / bound, 0.0, 26, S.SPFM_TI_GLOBAL)
+        with pytest.raises(S.SpfmError) as e:
+            S.spfm_step(h, 0, 1.0, 1.0, lam, 1.0, 1.001 * 2 / bound, 0.0, 26, S.SPFM_TI_GLOBAL)
+        assert e.value.status == S.SPFM_EUNSTABLE
+    finally:
+        S.spfm_destroy_grid(h)
+
+
+def test_last_error_is_thread_local_without_grid(lib):
+    with pytest.raises(S.SpfmError):
+        S.spfm_layout(_desc(dtype=9))
+    assert "dtype" in S.spfm_last_error(None)

@@ -57,7 +57,7 @@ def test_init_planar_and_sphere(dtype):
     g, p = make_pair(45, 23, 9, dtype, (S.SPFM_CONTACT,) * 6, n, lam=2.5, dx=0.7)
     g.init_planar(7.1, 2.5, 0.7)
     ref = O.init_planar(p, 7.1)
-    tol = 2e-16 if dtype == S.SPFM_F64 else 6e-8
+    tol = 2e-15 if dtype == S.SPFM_F64 else 6e-8   # CUDA and libm tanh differ by a few ulps
     assert np.abs(gpu_field(g) - ref).max() <= tol
     ctr = (14.2, 8.1, 3.3)
     g.init_sphere(ctr, 6.0, 2.5, 0.7)
