@@ -26,11 +26,15 @@
  *    The library owns only its opaque host objects and never frees caller
  *    buffers.  Pointers named `field`, `scratch` and `dst`/`src` with
  *    *_on_host == 0 are device pointers of the current CUDA device.
- *  - Field layout in HBM: x fastest, element (i, j, k) at
- *    field[(k * ny + j) * pitch_x + i], pitch_x = nx rounded up to a multiple
- *    of 16 bytes worth of elements; every row starts 16-byte aligned.  The
- *    base pointer must be 16-byte aligned.  Padding elements are never read
- *    as data.
+ *  - Field layout in HBM: x fastest, with a one-cell ghost layer on every
+ *    face.  Interior cell (i, j, k), 0 <= i < nx etc., is
+ *      field[((k + 1) * (ny + 2) + (j + 1)) * pitch_x + x_off + i],
+ *    ghost cells sit at i = -1, nx, j = -1, ny, k = -1, nz.  x_off is 16 bytes
+ *    worth of elements (2 FP64, 4 FP32, 8 BF16), pitch_x a 16-byte multiple
+ *    >= x_off + nx + 1, so every interior row starts 16-byte aligned.  The
+ *    base pointer must be 16-byte aligned.  The library keeps the ghosts
+ *    consistent with the boundary conditions; use spfm_get_field /
+ *    spfm_set_field to exchange dense interior arrays.
  *  - Launches are asynchronous on the grid's stream.  spfm_interface_stats,
  *    spfm_get_field (to host) and spfm_batch_stats synchronise that stream.
  */
@@ -97,10 +101,13 @@ typedef struct {
     int stencil, scheme;
 } spfm_step_args;
 
-/* Layout of a grid: pitch_x (elements), bytes of ONE field buffer and bytes of
- * scratch the caller must provide.  Any output pointer may be NULL. */
-spfm_status spfm_layout(const spfm_grid_desc *desc, size_t *pitch_x, size_t *field_bytes,
-                        size_t *scratch_bytes);
+/* Layout of a grid: pitch_x and x_off (elements), bytes of ONE field buffer
+ * and bytes of scratch the caller must provide.  Any output pointer may be NULL.
+ * The scratch holds the stats reduction and a device error word that the step
+ * kernels set when a bounded wait gives up (reported by spfm_interface_stats
+ * as SPFM_ETIMEOUT). */
+spfm_status spfm_layout(const spfm_grid_desc *desc, size_t *pitch_x, size_t *x_off,
+                        size_t *field_bytes, size_t *scratch_bytes);
 
 /* Validate desc and create the host handle.  The handle borrows the buffers. */
 spfm_status spfm_create_grid(const spfm_grid_desc *desc, spfm_grid **out);
@@ -126,11 +133,15 @@ spfm_status spfm_step(spfm_grid *g, int n_steps, double M, double Gamma, double 
 /* FP64 interface diagnostics of the current field (Sec. 2.3 inversion of the
  * ideal profile); flags may include SPFM_STATS_ENERGY.  Uses the model of the
  * last spfm_step (or lambda/dx of the last init).  Synchronises the stream.
- * Returns SPFM_ENONFINITE (with *out filled) if the field holds NaN/Inf. */
+ * Returns SPFM_ETIMEOUT if a step kernel's bounded wait gave up since the last
+ * init/set_field, else SPFM_ENONFINITE (with *out filled) if the field holds
+ * NaN/Inf. */
 spfm_status spfm_interface_stats(spfm_grid *g, int flags, spfm_stats *out);
 
-/* Copy the current field to/from a dense (nz, ny, nx) array of the storage
- * type; *_on_host selects a host or a device pointer. set_field resets steps. */
+/* Copy the interior of the current field to/from a dense (nz, ny, nx) array of
+ * the storage type; *_on_host selects a host or a device pointer.  set_field
+ * resets the step count and rebuilds the ghost layer (at the next step when no
+ * lambda is known yet). */
 spfm_status spfm_get_field(spfm_grid *g, void *dst, int dst_on_host);
 spfm_status spfm_set_field(spfm_grid *g, const void *src, int src_on_host);
 /* Index (0 or 1) of the buffer holding the current field. */

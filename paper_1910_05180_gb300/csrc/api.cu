@@ -24,6 +24,9 @@ struct spfm_grid {
     GridGeom geom;
     size_t elem;           // bytes per element
     int cur = 0;           // buffer holding the current field
+    bool ghosts_dirty = true;          // ghost layer of the current buffer needs a refill
+    double ghost_lambda = 0.0, ghost_dx = 0.0;   // model the ghosts were filled with
+    TmaCache tma;                      // tensor maps of the two buffers
     long long steps = 0;
     double time = 0.0;
     // model of the last step (stats: energy, estimator)
@@ -209,8 +212,8 @@ const char *spfm_last_error(const spfm_grid *g)
     return g ? g->err.c_str() : t_err.c_str();
 }
 
-spfm_status spfm_layout(const spfm_grid_desc *d, size_t *pitch_x, size_t *field_bytes,
-                        size_t *scratch_bytes)
+spfm_status spfm_layout(const spfm_grid_desc *d, size_t *pitch_x, size_t *x_offset,
+                        size_t *field_bytes, size_t *scratch_bytes)
 {
     if (!d) return fail(nullptr, SPFM_EINVAL, "spfm_layout: desc is NULL");
     if (d->nx < 1 || d->ny < 1 || d->nz < 1)
@@ -218,10 +221,11 @@ spfm_status spfm_layout(const spfm_grid_desc *d, size_t *pitch_x, size_t *field_
     if (d->dtype != SPFM_F64 && d->dtype != SPFM_F32 && d->dtype != SPFM_BF16)
         return fail(nullptr, SPFM_EINVAL, "spfm_layout: unknown dtype %d", d->dtype);
     const size_t es = elem_size(d->dtype), per16 = 16 / es;
-    const size_t px = (d->nx + per16 - 1) / per16 * per16;
+    const size_t px = (per16 + d->nx + 1 + per16 - 1) / per16 * per16;
     if (pitch_x) *pitch_x = px;
-    if (field_bytes) *field_bytes = px * (size_t)d->ny * (size_t)d->nz * es;
-    if (scratch_bytes) *scratch_bytes = stats_scratch_bytes();
+    if (x_offset) *x_offset = per16;
+    if (field_bytes) *field_bytes = px * (size_t)(d->ny + 2) * (size_t)(d->nz + 2) * es;
+    if (scratch_bytes) *scratch_bytes = grid_scratch_bytes();
     return SPFM_OK;
 }
 
@@ -229,10 +233,10 @@ spfm_status spfm_create_grid(const spfm_grid_desc *d, spfm_grid **out)
 {
     if (!out) return fail(nullptr, SPFM_EINVAL, "spfm_create_grid: out is NULL");
     *out = nullptr;
-    size_t px = 0, fb = 0, sb = 0;
-    spfm_status st = spfm_layout(d, &px, &fb, &sb);
+    size_t px = 0, off = 0, fb = 0, sb = 0;
+    spfm_status st = spfm_layout(d, &px, &off, &fb, &sb);
     if (st != SPFM_OK) return st;
-    if ((long long)px * d->ny * (long long)d->nz >= (1LL << 40))
+    if ((long long)px * (d->ny + 2) * (long long)(d->nz + 2) >= (1LL << 40))
         return fail(nullptr, SPFM_EINVAL, "spfm_create_grid: grid too large");
     for (int f = 0; f < 6; ++f)
         if (d->bc[f] != SPFM_PERIODIC && d->bc[f] != SPFM_NOFLUX && d->bc[f] != SPFM_CONTACT)
@@ -253,13 +257,15 @@ spfm_status spfm_create_grid(const spfm_grid_desc *d, spfm_grid **out)
     if (d->C_gamma < 0.0 || d->gamma[0] < 0.0 || d->gamma[1] < 0.0 || d->gamma[2] < 0.0)
         return fail(nullptr, SPFM_EINVAL, "spfm_create_grid: negative gamma or C_gamma");
     spfm_grid *g = new spfm_grid();
+    memset(&g->tma, 0, sizeof g->tma);
     g->d = *d;
     g->elem = elem_size(d->dtype);
     g->geom.nx = d->nx;
     g->geom.ny = d->ny;
     g->geom.nz = d->nz;
     g->geom.pitch = (int)px;
-    g->geom.plane = (long long)px * d->ny;
+    g->geom.off = (int)off;
+    g->geom.plane = (long long)px * (d->ny + 2);
     for (int f = 0; f < 6; ++f) g->geom.bc[f] = d->bc[f];
     *out = g;
     return SPFM_OK;
@@ -280,6 +286,28 @@ spfm_status spfm_set_stream(spfm_grid *g, void *stream)
 
 int spfm_current(const spfm_grid *g) { return g ? g->cur : -1; }
 
+// Refill the ghost layer of the current buffer for the given lambda and dx
+// (contact faces depend on both), and clear the device error word.
+static spfm_status refresh_ghosts(spfm_grid *g, double lambda, double dx)
+{
+    double af[6];
+    for (int f = 0; f < 6; ++f) {
+        const double sgn = (f % 2 == 0) ? -1.0 : 1.0;
+        af[f] = tanh(2.0 * sgn * dx * g->d.n[f / 2] / lambda);
+    }
+    cudaError_t e = launch_fill_ghosts(g->geom, g->d.dtype, af, g->d.field[g->cur], stream_of(g));
+    if (e != cudaSuccess) return cuda_fail(g, e, "ghost fill");
+    g->ghosts_dirty = false;
+    g->ghost_lambda = lambda;
+    g->ghost_dx = dx;
+    return SPFM_OK;
+}
+
+static int *err_word(const spfm_grid *g)
+{
+    return (int *)((char *)g->d.scratch + scratch_err_offset());
+}
+
 static spfm_status init_common(spfm_grid *g, InitArgs &a, double lambda, double dx)
 {
     if (!(lambda > 0.0) || !(dx > 0.0))
@@ -290,12 +318,13 @@ static spfm_status init_common(spfm_grid *g, InitArgs &a, double lambda, double 
     a.dx = dx;
     g->cur = 0;
     cudaError_t e = launch_init(a, g->d.field[0], stream_of(g));
+    if (e == cudaSuccess) e = cudaMemsetAsync(err_word(g), 0, sizeof(int), stream_of(g));
     if (e != cudaSuccess) return cuda_fail(g, e, "spfm_init");
     g->steps = 0;
     g->time = 0.0;
     g->lambda = lambda;
     g->dx = dx;
-    return SPFM_OK;
+    return refresh_ghosts(g, lambda, dx);
 }
 
 spfm_status spfm_init_planar(spfm_grid *g, double c, double lambda, double dx)
@@ -331,12 +360,20 @@ spfm_status spfm_step(spfm_grid *g, int n_steps, double M, double Gamma, double 
         return fail(g, SPFM_EINVAL, "spfm_step: SPFM_TI_LOCAL is not available in this build");
     const LaunchCfg cfg{stencil, scheme};
     cudaStream_t s = stream_of(g);
+    if (n_steps > 0 && (g->ghosts_dirty || g->ghost_lambda != lambda || g->ghost_dx != dx)) {
+        st = refresh_ghosts(g, lambda, dx);
+        if (st != SPFM_OK) return st;
+    }
+    int *err = err_word(g);
     if (g->d.dtype == SPFM_F64) {
         StepCoef<double> c;
         fill_coef<double>(g, m, dt, c);
         for (int i = 0; i < n_steps; ++i) {
             cudaError_t e = launch_step_f64(c, (const double *)g->d.field[g->cur],
-                                            (double *)g->d.field[1 - g->cur], cfg, s);
+                                            (double *)g->d.field[1 - g->cur], err, cfg, &g->tma,
+                                            g->cur, s);
+            if (e == cudaSuccess)
+                e = launch_fill_ghosts(g->geom, g->d.dtype, m.aface, g->d.field[1 - g->cur], s);
             if (e != cudaSuccess) return cuda_fail(g, e, "spfm_step");
             g->cur ^= 1;
         }
@@ -346,10 +383,14 @@ spfm_status spfm_step(spfm_grid *g, int n_steps, double M, double Gamma, double 
         for (int i = 0; i < n_steps; ++i) {
             cudaError_t e;
             if (g->d.dtype == SPFM_F32)
-                e = launch_step_f32(c, (const float *)g->d.field[g->cur], (float *)g->d.field[1 - g->cur], cfg, s);
+                e = launch_step_f32(c, (const float *)g->d.field[g->cur], (float *)g->d.field[1 - g->cur],
+                                    err, cfg, &g->tma, g->cur, s);
             else
                 e = launch_step_bf16(c, (const __nv_bfloat16 *)g->d.field[g->cur],
-                                     (__nv_bfloat16 *)g->d.field[1 - g->cur], cfg, s);
+                                     (__nv_bfloat16 *)g->d.field[1 - g->cur], err, cfg, &g->tma,
+                                     g->cur, s);
+            if (e == cudaSuccess)
+                e = launch_fill_ghosts(g->geom, g->d.dtype, m.aface, g->d.field[1 - g->cur], s);
             if (e != cudaSuccess) return cuda_fail(g, e, "spfm_step");
             g->cur ^= 1;
         }
@@ -391,19 +432,21 @@ spfm_status spfm_interface_stats(spfm_grid *g, int flags, spfm_stats *out)
         a.w[k] = k < nd ? gam[d.shell - 1] * nu[d.shell - 1] : 0.0;
         a.a[k] = tanh(2.0 * g->dx * (d.x * g->d.n[0] + d.y * g->d.n[1] + d.z * g->d.n[2]) / g->lambda);
     }
-    for (int f = 0; f < 6; ++f) {
-        const double sgn = (f % 2 == 0) ? -1.0 : 1.0;
-        a.aface[f] = tanh(2.0 * sgn * g->dx * g->d.n[f / 2] / g->lambda);
+    if (a.energy && (g->ghosts_dirty || g->ghost_lambda != g->lambda || g->ghost_dx != g->dx)) {
+        spfm_status st = refresh_ghosts(g, g->lambda, g->dx);
+        if (st != SPFM_OK) return st;
     }
     double *partials = (double *)g->d.scratch;
-    double *fin = partials + (size_t)kNStat * kStatsBlocks;
+    double *fin = (double *)((char *)g->d.scratch + scratch_final_offset());
     cudaStream_t s = stream_of(g);
     cudaError_t e = launch_stats(a, g->d.field[g->cur], partials, fin, s);
     if (e != cudaSuccess) return cuda_fail(g, e, "spfm_interface_stats");
-    double h[kNStat];
+    double h[kNStat + 1];   // the reduction, then the error word
     e = cudaMemcpyAsync(h, fin, sizeof h, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(g, e, "spfm_interface_stats");
+    int errw;
+    memcpy(&errw, &h[kNStat], sizeof errw);
     out->volume = h[0] * g->dx * g->dx * g->dx;
     out->S_w = h[1];
     out->S_c = h[2];
@@ -416,6 +459,8 @@ spfm_status spfm_interface_stats(spfm_grid *g, int flags, spfm_stats *out)
     out->energy = a.energy ? h[7] * g->dx * g->dx * g->dx : NAN;
     out->steps = (double)g->steps;
     out->time = g->time;
+    if (errw != 0)
+        return fail(g, SPFM_ETIMEOUT, "a bounded wait in the step kernel gave up (code %d)", errw);
     if (h[6] > 0.0) return fail(g, SPFM_ENONFINITE, "field holds %.0f non-finite cells", h[6]);
     return SPFM_OK;
 }
@@ -423,17 +468,28 @@ spfm_status spfm_interface_stats(spfm_grid *g, int flags, spfm_stats *out)
 static spfm_status copy_field(spfm_grid *g, void *host_or_dev, int on_host, int to_grid)
 {
     const size_t es = g->elem;
-    const size_t row = (size_t)g->d.nx * es, pitch = (size_t)g->geom.pitch * es;
-    const size_t rows = (size_t)g->d.ny * g->d.nz;
-    cudaStream_t s = stream_of(g);
-    cudaError_t e;
+    cudaMemcpy3DParms p;
+    memset(&p, 0, sizeof p);
+    const cudaPitchedPtr grid_ptr =
+        make_cudaPitchedPtr(g->d.field[g->cur], (size_t)g->geom.pitch * es, (size_t)g->geom.pitch * es,
+                            (size_t)g->d.ny + 2);
+    const cudaPitchedPtr dense_ptr =
+        make_cudaPitchedPtr(host_or_dev, (size_t)g->d.nx * es, (size_t)g->d.nx * es, (size_t)g->d.ny);
+    const cudaPos interior = make_cudaPos((size_t)g->geom.off * es, 1, 1);
+    p.extent = make_cudaExtent((size_t)g->d.nx * es, (size_t)g->d.ny, (size_t)g->d.nz);
     if (to_grid) {
-        e = cudaMemcpy2DAsync(g->d.field[g->cur], pitch, host_or_dev, row, row, rows,
-                              on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s);
+        p.srcPtr = dense_ptr;
+        p.dstPtr = grid_ptr;
+        p.dstPos = interior;
+        p.kind = on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     } else {
-        e = cudaMemcpy2DAsync(host_or_dev, row, g->d.field[g->cur], pitch, row, rows,
-                              on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s);
+        p.srcPtr = grid_ptr;
+        p.srcPos = interior;
+        p.dstPtr = dense_ptr;
+        p.kind = on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     }
+    cudaStream_t s = stream_of(g);
+    cudaError_t e = cudaMemcpy3DAsync(&p, s);
     if (e == cudaSuccess && on_host) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(g, e, to_grid ? "spfm_set_field" : "spfm_get_field");
     return SPFM_OK;
@@ -449,8 +505,14 @@ spfm_status spfm_set_field(spfm_grid *g, const void *src, int src_on_host)
 {
     if (!g || !src) return fail(g, SPFM_EINVAL, "spfm_set_field: NULL argument");
     spfm_status st = copy_field(g, const_cast<void *>(src), src_on_host, 1);
-    if (st == SPFM_OK) { g->steps = 0; g->time = 0.0; }
-    return st;
+    if (st != SPFM_OK) return st;
+    g->steps = 0;
+    g->time = 0.0;
+    g->ghosts_dirty = true;   // refilled by the next step, or now when lambda is known
+    cudaError_t e = cudaMemsetAsync(err_word(g), 0, sizeof(int), stream_of(g));
+    if (e != cudaSuccess) return cuda_fail(g, e, "spfm_set_field");
+    if (g->lambda > 0.0) return refresh_ghosts(g, g->lambda, g->dx);
+    return SPFM_OK;
 }
 
 }  // extern "C"

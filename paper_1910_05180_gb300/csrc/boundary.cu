@@ -1,0 +1,93 @@
+// boundary.cu -- refresh of the ghost layer from the interior.
+//
+// Every ghost cell takes the value of the interior cell its boundary map
+// points at (periodic wrap, no-flux copy of the adjacent cell), shifted by
+// Eq. 7 with the signed coupling a = tanh(2 (x_ghost - x_source).n / lambda) on
+// contact faces.  A ghost outside several faces maps every outside coordinate
+// at once; the shifts compose in any order because each is a translation of
+// the ideal profile, so no face has to be filled before another.
+//
+// The ghost cells are enumerated face by face so that consecutive threads
+// touch consecutive x where the face allows it:
+//   z faces  k in {-1, nz}, all (i, j) in [-1, nx] x [-1, ny]
+//   y faces  j in {-1, ny}, (i, k) in [-1, nx] x [0, nz)
+//   x faces  i in {-1, nx}, (j, k) in [0, ny) x [0, nz)
+// One launch after every step (arithmetic in the step kernels' compute type).
+#include "spfm_internal.h"
+
+namespace spfm {
+
+template <class S> struct Cmp { using T = float; };
+template <> struct Cmp<double> { using T = double; };
+__device__ __forceinline__ double ld_ct(const double *f, long long i) { return f[i]; }
+__device__ __forceinline__ float ld_ct(const float *f, long long i) { return f[i]; }
+__device__ __forceinline__ float ld_ct(const __nv_bfloat16 *f, long long i) { return __bfloat162float(f[i]); }
+__device__ __forceinline__ void st_ct(double *f, long long i, double v) { f[i] = v; }
+__device__ __forceinline__ void st_ct(float *f, long long i, float v) { f[i] = v; }
+__device__ __forceinline__ void st_ct(__nv_bfloat16 *f, long long i, float v) { f[i] = __float2bfloat16_rn(v); }
+
+struct FaceArgs {
+    GridGeom g;
+    double aface[6];
+    long long nzf, nyf, nxf;   // ghost counts of the z, y and x faces (both sides)
+};
+
+template <class S>
+__global__ void __launch_bounds__(256) ghost_kernel(const FaceArgs a, S *f)
+{
+    using T = typename Cmp<S>::T;
+    const GridGeom &g = a.g;
+    const long long total = a.nzf + a.nyf + a.nxf;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        if (t < a.nzf) {
+            const long long per = (long long)(g.nx + 2) * (g.ny + 2);
+            const long long r = t % per;
+            k = t < per ? -1 : g.nz;
+            j = (int)(r / (g.nx + 2)) - 1;
+            i = (int)(r % (g.nx + 2)) - 1;
+        } else if (t < a.nzf + a.nyf) {
+            const long long u = t - a.nzf, per = (long long)(g.nx + 2) * g.nz;
+            const long long r = u % per;
+            j = u < per ? -1 : g.ny;
+            k = (int)(r / (g.nx + 2));
+            i = (int)(r % (g.nx + 2)) - 1;
+        } else {
+            const long long u = t - a.nzf - a.nyf, per = (long long)g.ny * g.nz;
+            const long long r = u % per;
+            i = u < per ? -1 : g.nx;
+            k = (int)(r / g.ny);
+            j = (int)(r % g.ny);
+        }
+        int fx, fy, fz;
+        const int sx = map_axis(i, g.nx, g.bc[0], g.bc[1], &fx, 0);
+        const int sy = map_axis(j, g.ny, g.bc[2], g.bc[3], &fy, 2);
+        const int sz = map_axis(k, g.nz, g.bc[4], g.bc[5], &fz, 4);
+        T v = ld_ct(f, cell_index(g, sx, sy, sz));
+        if (fx >= 0) v = contact_shift<T>(v, (T)a.aface[fx]);
+        if (fy >= 0) v = contact_shift<T>(v, (T)a.aface[fy]);
+        if (fz >= 0) v = contact_shift<T>(v, (T)a.aface[fz]);
+        st_ct(f, cell_index(g, i, j, k), v);
+    }
+}
+
+cudaError_t launch_fill_ghosts(const GridGeom &g, int dtype, const double aface[6], void *field,
+                               cudaStream_t st)
+{
+    FaceArgs a;
+    a.g = g;
+    for (int f = 0; f < 6; ++f) a.aface[f] = aface[f];
+    a.nzf = 2LL * (g.nx + 2) * (g.ny + 2);
+    a.nyf = 2LL * (g.nx + 2) * g.nz;
+    a.nxf = 2LL * g.ny * g.nz;
+    const long long total = a.nzf + a.nyf + a.nxf;
+    long long blocks = (total + 255) / 256;
+    if (blocks > 2 * 152 * 8) blocks = 2 * 152 * 8;
+    if (dtype == SPFM_F64) ghost_kernel<double><<<(int)blocks, 256, 0, st>>>(a, (double *)field);
+    else if (dtype == SPFM_F32) ghost_kernel<float><<<(int)blocks, 256, 0, st>>>(a, (float *)field);
+    else ghost_kernel<__nv_bfloat16><<<(int)blocks, 256, 0, st>>>(a, (__nv_bfloat16 *)field);
+    return cudaGetLastError();
+}
+
+}  // namespace spfm

@@ -5,6 +5,7 @@
 // declarations that connect the C ABI (api.cu) to the kernels.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -39,13 +40,23 @@ __host__ __device__ inline Dir grid_dir(int k)
     }
 }
 
-// Geometry of one grid as the kernels see it.
+// Geometry of one grid buffer as the kernels see it.  Every buffer carries a
+// one-cell ghost layer: interior cell (i, j, k), i in [0, nx), sits at
+//   ((k + 1) * (ny + 2) + (j + 1)) * pitch + off + i,
+// ghosts at i = -1, nx, j = -1, ny, k = -1, nz.  off = 16 bytes of elements, so
+// interior rows start 16-byte aligned; pitch is a 16-byte multiple >= off + nx + 1.
 struct GridGeom {
     int nx, ny, nz;
-    int pitch;          // elements per row (16-byte multiple)
-    long long plane;    // pitch * ny
+    int pitch;          // elements per padded row
+    int off;            // x offset of interior cell 0 (16 bytes of elements)
+    long long plane;    // pitch * (ny + 2)
     int bc[6];          // SPFM_PERIODIC / NOFLUX / CONTACT per face
 };
+
+__host__ __device__ inline long long cell_index(const GridGeom &g, int i, int j, int k)
+{
+    return (long long)(k + 1) * g.plane + (long long)(j + 1) * g.pitch + g.off + i;
+}
 
 // Step coefficients of one grid, precomputed on the host in FP64 (a1) and
 // rounded to the compute type T.
@@ -89,12 +100,6 @@ __host__ __device__ inline T contact_shift(T v, T a)
     return (T(1) - a) * v / (T(1) - a * (T(2) * v - T(1)));
 }
 
-template <class S> __host__ __device__ inline float to_f(S v);
-template <> __host__ __device__ inline float to_f<float>(float v) { return v; }
-template <> __host__ __device__ inline float to_f<__nv_bfloat16>(__nv_bfloat16 v)
-{
-    return __bfloat162float(v);
-}
 
 // ---------------------------------------------------------------- launchers
 
@@ -103,13 +108,32 @@ struct LaunchCfg {
     int scheme;    // SPFM_TI_GLOBAL, SPFM_TI_LOCAL, SPFM_FD
 };
 
+// TMA tensor maps of a grid's two field buffers, encoded on first use (tma.cu).
+struct TmaCache {
+    CUtensorMap map[2];
+    const void *base[2];
+    int state[2];   // 0 not encoded, 1 encoded, -1 encoding unavailable (row copies)
+};
+
+// Encode a 3D tiled map over a ghosted buffer with a (box_x, box_y, 1) box.
+// Returns 0 on success.
+int encode_field_map(CUtensorMap *map, const GridGeom &g, int dtype, const void *base, int box_x,
+                     int box_y);
+
+// The map of buffer `which` (base), encoded on demand; NULL when unavailable.
+const CUtensorMap *cached_map(TmaCache *cache, int which, const GridGeom &g, int dtype,
+                              const void *base, int box_x, int box_y);
+
 // One explicit step src -> dst of one grid (step_f32.cu / step_f64.cu / step_bf16.cu).
-cudaError_t launch_step_f32(const StepCoef<float> &c, const float *src, float *dst,
-                            LaunchCfg cfg, cudaStream_t st);
-cudaError_t launch_step_f64(const StepCoef<double> &c, const double *src, double *dst,
-                            LaunchCfg cfg, cudaStream_t st);
+// err: device word that a kernel sets when one of its bounded waits gives up.
+// tma: map cache of the grid (NULL: row-wise bulk copies); which: index of src.
+cudaError_t launch_step_f32(const StepCoef<float> &c, const float *src, float *dst, int *err,
+                            LaunchCfg cfg, TmaCache *tma, int which, cudaStream_t st);
+cudaError_t launch_step_f64(const StepCoef<double> &c, const double *src, double *dst, int *err,
+                            LaunchCfg cfg, TmaCache *tma, int which, cudaStream_t st);
 cudaError_t launch_step_bf16(const StepCoef<float> &c, const __nv_bfloat16 *src,
-                             __nv_bfloat16 *dst, LaunchCfg cfg, cudaStream_t st);
+                             __nv_bfloat16 *dst, int *err, LaunchCfg cfg, TmaCache *tma, int which,
+                             cudaStream_t st);
 
 // Initial ideal profiles and FP64 diagnostics (stats.cu).
 struct InitArgs {
@@ -122,11 +146,14 @@ struct InitArgs {
 };
 cudaError_t launch_init(const InitArgs &a, void *field, cudaStream_t st);
 
+// Ghost layer of a whole buffer from its interior (after init / set_field).
+cudaError_t launch_fill_ghosts(const GridGeom &g, int dtype, const double aface[6], void *field,
+                               cudaStream_t st);
+
 struct StatsArgs {
     GridGeom g;
     int dtype;
     double n[3], ctr[3];
-    double aface[6];      // contact coupling per face (ghosts of the forward differences)
     double lambda, dx;
     int energy;           // 1: also accumulate the interface energy
     int scheme, stencil;  // energy model
@@ -138,6 +165,10 @@ struct StatsArgs {
 cudaError_t launch_stats(const StatsArgs &a, const void *field, double *partials,
                          double *final_out, cudaStream_t st);
 
+// Scratch of one grid: stats partials, the final reduction, then the error word.
 size_t stats_scratch_bytes();
+inline size_t scratch_final_offset() { return sizeof(double) * (size_t)kNStat * kStatsBlocks; }
+inline size_t scratch_err_offset() { return sizeof(double) * (size_t)kNStat * (kStatsBlocks + 1); }
+size_t grid_scratch_bytes();
 
 }  // namespace spfm

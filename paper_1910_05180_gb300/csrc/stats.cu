@@ -1,17 +1,18 @@
-// stats.cu -- ideal-profile initialisation and FP64 interface diagnostics.
+// stats.cu -- ideal-profile initialisation and FP64 interface
+// diagnostics on the ghosted field layout (spfm_internal.h).
 //
 // init: Eq. 3 (planar) or its radial form, evaluated in FP64 per cell and
-// rounded once to the storage type; padding elements are zeroed.
+// rounded once to the storage type (the caller then fills the ghost layer).
 //
-// stats: one pass over the field accumulating in FP64, per thread in a fixed
-// grid-stride order, then warp-shuffle and shared-memory block reductions into
+// stats: one pass over the interior accumulating in FP64, per thread in a
+// fixed row order, then warp-shuffle and shared-memory block reductions into
 // kStatsBlocks partials, then one CTA reducing the partials in a fixed order,
 // so the result is bit-reproducible for a given grid size.  Sums over the band
 // 1e-6 < phi < 1 - 1e-6 invert the ideal profile (Sec. 2.3):
 //   position  c = sum q (p.n - (lambda/2) artanh(1-2phi)) / sum q
 //   radius    R = sum q (|p - ctr| + (lambda/2) artanh(1-2phi)) / sum q
-// The optional interface energy is Eq. 1 at dF = 0 with forward differences
-// whose ghosts follow the boundary conditions.
+// The optional interface energy is Eq. 1 at dF = 0; its forward differences
+// read the ghost layer.
 #include <math.h>
 
 #include "spfm_internal.h"
@@ -37,14 +38,16 @@ template <> __device__ __forceinline__ __nv_bfloat16 wr<__nv_bfloat16>(double v)
 template <class S>
 __global__ void init_kernel(const InitArgs a, S *f)
 {
-    const long long rows = (long long)a.g.ny * a.g.nz;
+    const long long rows = (long long)(a.g.ny + 2) * (a.g.nz + 2);
     for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
-        const int j = (int)(row % a.g.ny);
-        const int k = (int)(row / a.g.ny);
-        S *r = f + (long long)k * a.g.plane + (long long)j * a.g.pitch;
-        for (int i = threadIdx.x; i < a.g.pitch; i += blockDim.x) {
+        const int j = (int)(row % (a.g.ny + 2)) - 1;
+        const int k = (int)(row / (a.g.ny + 2)) - 1;
+        S *r = f + row * a.g.pitch;
+        const bool inner = j >= 0 && j < a.g.ny && k >= 0 && k < a.g.nz;
+        for (int x = threadIdx.x; x < a.g.pitch; x += blockDim.x) {
+            const int i = x - a.g.off;
             double v = 0.0;
-            if (i < a.g.nx) {
+            if (inner && i >= 0 && i < a.g.nx) {
                 const double px = a.dx * i, py = a.dx * j, pz = a.dx * k;
                 if (a.sphere) {
                     const double rx = px - a.ctr[0], ry = py - a.ctr[1], rz = pz - a.ctr[2];
@@ -55,34 +58,19 @@ __global__ void init_kernel(const InitArgs a, S *f)
                     v = 0.5 * (1.0 - tanh(2.0 * (pn - a.c) / a.lambda));
                 }
             }
-            r[i] = wr<S>(v);
+            r[x] = wr<S>(v);
         }
     }
 }
 
 cudaError_t launch_init(const InitArgs &a, void *field, cudaStream_t st)
 {
-    const long long rows = (long long)a.g.ny * a.g.nz;
+    const long long rows = (long long)(a.g.ny + 2) * (a.g.nz + 2);
     const int blocks = (int)(rows < 8192 ? rows : 8192);
     if (a.dtype == SPFM_F64) init_kernel<double><<<blocks, 128, 0, st>>>(a, (double *)field);
     else if (a.dtype == SPFM_F32) init_kernel<float><<<blocks, 128, 0, st>>>(a, (float *)field);
     else init_kernel<__nv_bfloat16><<<blocks, 128, 0, st>>>(a, (__nv_bfloat16 *)field);
     return cudaGetLastError();
-}
-
-// element with boundary ghosts (one cell outside per axis), FP64
-template <class S>
-__device__ double ghost_value(const StatsArgs &a, const S *f, int x, int y, int z)
-{
-    int fx, fy, fz;
-    const int sx = map_axis(x, a.g.nx, a.g.bc[0], a.g.bc[1], &fx, 0);
-    const int sy = map_axis(y, a.g.ny, a.g.bc[2], a.g.bc[3], &fy, 2);
-    const int sz = map_axis(z, a.g.nz, a.g.bc[4], a.g.bc[5], &fz, 4);
-    double v = rd<S>(f, (long long)sz * a.g.plane + (long long)sy * a.g.pitch + sx);
-    if (fx >= 0) v = contact_shift<double>(v, a.aface[fx]);
-    if (fy >= 0) v = contact_shift<double>(v, a.aface[fy]);
-    if (fz >= 0) v = contact_shift<double>(v, a.aface[fz]);
-    return v;
 }
 
 // Eq. 6 (TI) or the CF quartic per direction; lam2_r2 = lambda^2/|r_k|^2
@@ -126,6 +114,8 @@ __device__ __forceinline__ void block_reduce_store(double *v, double *out)
     }
 }
 
+// Per-thread partials: [0] sum phi, [1] S_w, [2] S_c, [3] S_r, [4] min, [5] max,
+// [6] non-finite count, [7] energy density sum, [8..11] unused.
 template <class S>
 __global__ void __launch_bounds__(256) stats_kernel(const StatsArgs a, const S *f, double *partials)
 {
@@ -136,14 +126,13 @@ __global__ void __launch_bounds__(256) stats_kernel(const StatsArgs a, const S *
     v[5] = -INFINITY;
     const double e_pref = a.Gamma / (a.C_gamma * a.lambda);
     const int nd = a.stencil == 6 ? 3 : (a.stencil == 18 ? 9 : 13);
-    // rows in a fixed grid-stride order, cells of a row across the threads
     const long long rows = (long long)a.g.ny * a.g.nz;
     for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
         const int j = (int)(row % a.g.ny);
         const int k = (int)(row / a.g.ny);
-        const S *fr = f + (long long)k * a.g.plane + (long long)j * a.g.pitch;
+        const long long rbase = cell_index(a.g, 0, j, k);
         for (int i = threadIdx.x; i < a.g.nx; i += blockDim.x) {
-            const double ph = rd<S>(fr, i);
+            const double ph = rd<S>(f, rbase + i);
             if (!isfinite(ph)) { v[6] += 1.0; continue; }
             v[0] += ph;
             v[4] = fmin(v[4], ph);
@@ -163,7 +152,7 @@ __global__ void __launch_bounds__(256) stats_kernel(const StatsArgs a, const S *
                 for (int kk = 0; kk < nd; ++kk) {
                     const Dir d = grid_dir(kk);
                     const double r2 = (double)d.shell * a.dx * a.dx;
-                    const double nb = ghost_value<S>(a, f, i + d.x, j + d.y, k + d.z);
+                    const double nb = rd<S>(f, cell_index(a.g, i + d.x, j + d.y, k + d.z));
                     const double dp = nb - ph;
                     e += a.w[kk] * (0.5 * a.lambda * a.lambda * dp * dp / r2 +
                                     potential(ph, a.a[kk], a.lambda * a.lambda / r2, a.scheme == SPFM_FD));
@@ -197,6 +186,11 @@ __global__ void __launch_bounds__(256) stats_final_kernel(const double *partials
 size_t stats_scratch_bytes()
 {
     return sizeof(double) * (size_t)kNStat * (kStatsBlocks + 1);
+}
+
+size_t grid_scratch_bytes()
+{
+    return scratch_err_offset() + 16;
 }
 
 cudaError_t launch_stats(const StatsArgs &a, const void *field, double *partials, double *final_out,

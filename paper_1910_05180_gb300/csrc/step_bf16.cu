@@ -2,9 +2,11 @@
 #include "step_kernel.cuh"
 
 namespace spfm {
-cudaError_t launch_step_bf16(const StepCoef<float> &c, const __nv_bfloat16 *src,
-                             __nv_bfloat16 *dst, LaunchCfg cfg, cudaStream_t st)
+cudaError_t launch_step_bf16(const StepCoef<float> &c, const __nv_bfloat16 *src, __nv_bfloat16 *dst, int *err,
+                            LaunchCfg cfg, TmaCache *tma, int which, cudaStream_t st)
 {
-    return launch_step_t<__nv_bfloat16, float, 8, 16>(c, src, dst, cfg, st);
+    using Sh = TileShape<__nv_bfloat16, float, 8, 16>;
+    const CUtensorMap *map = cached_map(tma, which, c.g, SPFM_BF16, src, Sh::SW, Sh::ROWS);
+    return launch_step_t<__nv_bfloat16, float, 8, 16>(c, src, dst, err, cfg, map, st);
 }
 }  // namespace spfm

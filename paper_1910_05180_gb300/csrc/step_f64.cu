@@ -2,9 +2,11 @@
 #include "step_kernel.cuh"
 
 namespace spfm {
-cudaError_t launch_step_f64(const StepCoef<double> &c, const double *src, double *dst,
-                            LaunchCfg cfg, cudaStream_t st)
+cudaError_t launch_step_f64(const StepCoef<double> &c, const double *src, double *dst, int *err,
+                            LaunchCfg cfg, TmaCache *tma, int which, cudaStream_t st)
 {
-    return launch_step_t<double, double, 16, 16>(c, src, dst, cfg, st);
+    using Sh = TileShape<double, double, 16, 16>;
+    const CUtensorMap *map = cached_map(tma, which, c.g, SPFM_F64, src, Sh::SW, Sh::ROWS);
+    return launch_step_t<double, double, 16, 16>(c, src, dst, err, cfg, map, st);
 }
 }  // namespace spfm

@@ -1,37 +1,48 @@
 // step_kernel.cuh -- z-marching 2.5D stencil kernel of one explicit SPFM / CF step.
 //
-// One CTA owns an xy tile of TX*VX by TY cells (VX = cells per 16 bytes) and
-// marches through a chunk of z planes.  Each arriving plane is staged, with a
-// one-cell halo whose ghost cells come from the boundary conditions, in a
-// double-buffered shared-memory tile, so one __syncthreads per plane suffices;
-// the next plane's 16-byte global loads are issued before the barrier and land
-// in registers while this plane is being used.  The x/y ghost mapping of every
-// load slot is resolved once per CTA; per plane only the z mapping changes.
+// Data movement.  Every field buffer carries a one-cell ghost layer in HBM
+// (spfm_internal.h), so a tile plus its halo is a set of plain, in-bounds,
+// 16-byte-aligned rows.  One CTA owns an xy tile of TX*VX by TY cells
+// (VX = cells per 16 bytes) and marches a chunk of z planes.  A producer warp
+// copies each plane's TY+2 halo rows into a ring of NS shared-memory stages
+// with bulk asynchronous copies (cp.async.bulk, completed on an mbarrier with
+// a transaction count); TX*TY consumer threads wait on the stage's "full"
+// barrier, read it, and release it on its "empty" barrier.  There is no
+// __syncthreads in the march, and NS-1 planes stay in flight per CTA.  Every
+// wait is bounded: on timeout the thread sets the error word and leaves.
 //
-// From each plane every thread forms, for its cells, three plane quantities:
+// Boundary conditions.  The kernel reads the ghost layer and writes interior
+// cells only; a separate face kernel (boundary.cu) refreshes the ghosts of the
+// new field after each step, so the hot path holds no boundary logic.
+//
+// Arithmetic.  From each plane every thread forms, for its cells,
 //   C  = phi at the cell,
 //   F' = sum of the 4 in-plane face neighbours minus C (each as a difference),
 //   E' = sum of the 4 in-plane diagonal neighbours minus C,
 // kept in registers for the planes z-1, z, z+1 (the z loop is unrolled by
-// three with rotating register roles, so nothing is copied between planes).
-// The shell sums of the 27-point stencil then follow without re-reading:
+// three with rotating register roles).  The shell sums then follow:
 //   S1 - 6 phi  = F'_z + t,             t = (C_{z-1} - phi) + (C_{z+1} - phi)
 //   S2 - 12 phi = E'_z + F'_{z-1} + F'_{z+1} + 4 t
 //   S3 - 8 phi  = E'_{z-1} + E'_{z+1} + 4 t
 // Every term is a difference of neighbouring values, which keeps FP32 drift far
-// below a plain sum of neighbours.
-//
-// FP32 arithmetic runs on packed f32x2 pairs (FFMA2/FADD2/FMUL2 of sm_100+).  A
-// thread's four cells x..x+3 form the packs A = (x, x+2) and B = (x+1, x+3);
-// shared memory holds every 16-byte quad in the order (v0, v2, v1, v3), so one
-// 128-bit shared load yields both packs in aligned register pairs and the
-// x-neighbour packs are W(A) = (x-1, x+1), E(A) = B, W(B) = A, E(B) = (x+2, x+4).
-// FP64 runs on scalar doubles with the same structure.
+// below a plain sum of neighbours.  FP32 runs on packed f32x2 pairs
+// (FFMA2/FADD2/FMUL2 of sm_100+) of adjacent cells; FP64 on scalar doubles.
 #pragma once
+
+#include <cuda.h>   // CUtensorMap (the map is encoded on the host, see tma.cu)
 
 #include "spfm_internal.h"
 
 namespace spfm {
+
+constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz per bounded wait
+
+#ifndef SPFM_STAGES
+#define SPFM_STAGES 4         // planes in flight per CTA
+#endif
+#ifndef SPFM_MIN_CTAS
+#define SPFM_MIN_CTAS 2       // resident CTAs per SM the register budget is sized for
+#endif
 
 // ------------------------------------------------------------ pack arithmetic
 
@@ -106,9 +117,9 @@ template <class S, class T> struct Io;
 
 template <> struct Io<float, float> {
     static constexpr int VX = 4;
-    static __device__ __forceinline__ void ld(const float *p, float *v)
+    static __device__ __forceinline__ void lds(const float *p, float *v)   // 16 B of shared
     {
-        float4 r = __ldg(reinterpret_cast<const float4 *>(p));
+        const float4 r = *reinterpret_cast<const float4 *>(p);
         v[0] = r.x; v[1] = r.y; v[2] = r.z; v[3] = r.w;
     }
     static __device__ __forceinline__ void st(float *p, const float *v)
@@ -121,9 +132,9 @@ template <> struct Io<float, float> {
 
 template <> struct Io<double, double> {
     static constexpr int VX = 2;
-    static __device__ __forceinline__ void ld(const double *p, double *v)
+    static __device__ __forceinline__ void lds(const double *p, double *v)
     {
-        double2 r = __ldg(reinterpret_cast<const double2 *>(p));
+        const double2 r = *reinterpret_cast<const double2 *>(p);
         v[0] = r.x; v[1] = r.y;
     }
     static __device__ __forceinline__ void st(double *p, const double *v)
@@ -136,9 +147,9 @@ template <> struct Io<double, double> {
 
 template <> struct Io<__nv_bfloat16, float> {
     static constexpr int VX = 8;
-    static __device__ __forceinline__ void ld(const __nv_bfloat16 *p, float *v)
+    static __device__ __forceinline__ void lds(const __nv_bfloat16 *p, float *v)
     {
-        uint4 r = __ldg(reinterpret_cast<const uint4 *>(p));
+        const uint4 r = *reinterpret_cast<const uint4 *>(p);
         const uint32_t w[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -160,148 +171,88 @@ template <> struct Io<__nv_bfloat16, float> {
     static __device__ __forceinline__ __nv_bfloat16 cvt_out(float t) { return __float2bfloat16_rn(t); }
 };
 
-// ------------------------------------------------------------- load slots
+// --------------------------------------------------------------- mbarrier
 
-// One staged load of a plane: a row of VX cells (or one cell) whose x/y ghost
-// mapping is fixed for the whole z march.
-struct Slot {
-    long long row;   // sy * pitch (+ gx when xfull)
-    int gx;          // first x of the slot
-    int yface;       // contact face of the y mapping, or -1
-    int mode;        // 0 inactive (value unused), 1 full vector in range, 2 per element
-};
-
-__device__ __forceinline__ Slot make_slot(const GridGeom &g, int gx, int gy, int width)
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
-    Slot s;
-    s.gx = gx;
-    s.yface = -1;
-    if (gy < -1 || gy > g.ny || gx > g.nx || gx + width - 1 < -1) {
-        s.mode = 0;
-        s.row = 0;
-        return s;
-    }
-    const int sy = map_axis(gy, g.ny, g.bc[2], g.bc[3], &s.yface, 2);
-    s.row = (long long)sy * g.pitch;
-    if (gx >= 0 && gx + width <= g.nx) {
-        s.mode = 1;
-        s.row += gx;
-    } else {
-        s.mode = 2;
-    }
-    return s;
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Loads the slot's `width` cells of plane (already z-mapped) `pbase`, applying
-// the ghost maps of x (per element), y (per slot) and z (per plane).
-template <class S, class T, int WIDTH>
-__device__ __forceinline__ void load_slot(const StepCoef<T> &C, const S *__restrict__ pbase,
-                                          const Slot &s, int zface, T *out)
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
-    if (s.mode == 1) {
-        if (WIDTH == 1) out[0] = Io<S, T>::cvt_in(pbase[s.row]);
-        else Io<S, T>::ld(pbase + s.row, out);
-    } else if (s.mode == 2) {
-#pragma unroll
-        for (int e = 0; e < WIDTH; ++e) {
-            const int gx = s.gx + e;
-            T v = T(0);
-            if (gx >= -1 && gx <= C.g.nx) {
-                int fx;
-                const int sx = map_axis(gx, C.g.nx, C.g.bc[0], C.g.bc[1], &fx, 0);
-                v = Io<S, T>::cvt_in(pbase[s.row + sx]);
-                if (fx >= 0) v = contact_shift<T>(v, C.aface[fx]);
-            }
-            out[e] = v;
-        }
-    } else {
-#pragma unroll
-        for (int e = 0; e < WIDTH; ++e) out[e] = T(0);
-    }
-    if (s.yface >= 0) {
-#pragma unroll
-        for (int e = 0; e < WIDTH; ++e) out[e] = contact_shift<T>(out[e], C.aface[s.yface]);
-    }
-    if (zface >= 0) {
-#pragma unroll
-        for (int e = 0; e < WIDTH; ++e) out[e] = contact_shift<T>(out[e], C.aface[zface]);
-    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
-// ------------------------------------------------------ shared-memory rows
-
-// Shared rows hold quads of 4 cells in the order (v0, v2, v1, v3) for VX >= 4.
-template <class T, int VX>
-__device__ __forceinline__ void put_row(T *dst, const T *v)
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
 {
-    if constexpr (VX == 2) {
-        dst[0] = v[0];
-        dst[1] = v[1];
-    } else {
-#pragma unroll
-        for (int q = 0; q < VX / 4; ++q) {
-            if constexpr (sizeof(T) == 4) {
-                *reinterpret_cast<float4 *>(dst + 4 * q) =
-                    make_float4(v[4 * q], v[4 * q + 2], v[4 * q + 1], v[4 * q + 3]);
-            } else {
-                dst[4 * q] = v[4 * q];
-                dst[4 * q + 1] = v[4 * q + 2];
-                dst[4 * q + 2] = v[4 * q + 1];
-                dst[4 * q + 3] = v[4 * q + 3];
-            }
-        }
-    }
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
 }
 
-// The packs of one shared row around a thread's cells: C[p], W[p], E[p].
-template <class T, int VX>
-struct RowPacks {
-    using P = typename Pk<T>::P;
-    static constexpr int NP = VX / 2;
-    P c[NP], w[NP], e[NP];
-};
-
-template <class T, int VX>
-__device__ __forceinline__ void get_row(const T *r, RowPacks<T, VX> &o)
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
-    using K = Pk<T>;
-    if constexpr (VX == 2) {
-        const T l = r[-1], v0 = r[0], v1 = r[1], rr = r[2];
-        o.c[0] = K::mk(v0, v1);
-        o.w[0] = K::mk(l, v0);
-        o.e[0] = K::mk(v1, rr);
-    } else {
-        constexpr int NQ = VX / 4;
-        typename Pk<T>::P a[NQ], b[NQ];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            if constexpr (sizeof(T) == 4) {
-                const float4 f = *reinterpret_cast<const float4 *>(r + 4 * q);
-                a[q] = K::mk(f.x, f.y);   // (v0, v2)
-                b[q] = K::mk(f.z, f.w);   // (v1, v3)
-            } else {
-                a[q] = K::mk(r[4 * q], r[4 * q + 1]);
-                b[q] = K::mk(r[4 * q + 2], r[4 * q + 3]);
-            }
-        }
-        const T l = r[-1], rr = r[VX];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            o.c[2 * q] = a[q];
-            o.c[2 * q + 1] = b[q];
-            o.w[2 * q] = K::mk(q == 0 ? l : b[q - 1].y, b[q].x);          // (x-1, x+1)
-            o.e[2 * q] = b[q];                                            // (x+1, x+3)
-            o.w[2 * q + 1] = a[q];                                        // (x,   x+2)
-            o.e[2 * q + 1] = K::mk(a[q].y, q == NQ - 1 ? rr : a[q + 1].x);  // (x+2, x+4)
-        }
-    }
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// cell index (0..VX-1) of lane `lane` of pack p
-template <int VX>
-__device__ __forceinline__ constexpr int pack_cell(int p, int lane)
+// One test of the phase; a thread whose phase is not complete is suspended in
+// hardware for up to the hint (ns) instead of spinning on issue slots.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {
-    return VX == 2 ? p * 2 + lane : (p / 2) * 4 + (p % 2) + 2 * lane;
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(1000000u)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the barrier phase with the given parity; false after ~2 s.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kWaitCycles) return false;
+    return true;
+}
+
+// Bulk asynchronous copy global -> shared, completing bytes on bar.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Producer-side wait: polls with a nanosleep back-off so a waiting producer does
+// not take issue slots from the consumers; false after ~2 s.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    unsigned ns = 32;
+    while (!mbar_try_wait(bar, parity)) {
+        __nanosleep(ns);
+        ns = ns < 256 ? 2 * ns : 256;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+    return true;
+}
+
+// TMA tile copy of a 3D box (x, y, z start in elements) into shared memory.
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
 }
 
 // -------------------------------------------------------------------- tile
@@ -311,9 +262,13 @@ struct TileShape {
     static constexpr int VX = Io<S, T>::VX;
     static constexpr int NP = VX / 2;
     static constexpr int W = TX * VX;
-    static constexpr int SW = W + 2 * VX;   // interior starts at VX (16-byte aligned)
+    static constexpr int SW = W + 2 * VX;   // staged row: one 16-byte chunk of halo per side
     static constexpr int ROWS = TY + 2;
-    static constexpr int SMEM_ELEMS = 2 * ROWS * SW;
+    static constexpr int BOX_BYTES = ROWS * SW * (int)sizeof(S);          // one TMA box
+    static constexpr int STAGE = ((BOX_BYTES + 127) / 128 * 128) / (int)sizeof(S);   // 128-B aligned
+    static constexpr int NS = SPFM_STAGES;  // pipeline depth (planes)
+    static constexpr int NCONS = TX * TY;   // consumer threads
+    static constexpr int NTHREADS = NCONS + 32;
 };
 
 template <class T, int NP>
@@ -322,80 +277,115 @@ struct PlaneQ {
     P c[NP], f[NP], e[NP];
 };
 
-// KIND: 0 = CF potential, 1 = TI global with <= 4 groups, 2 = TI global <= 13 groups
+// The packs of one staged row around a thread's cells (adjacent pairs):
+// c[p] = (x+2p, x+2p+1), w[p] = c shifted by -1, e[p] = shifted by +1.
+template <class S, class T, int VX>
+__device__ __forceinline__ void get_row(const S *r, typename Pk<T>::P *c, typename Pk<T>::P *w,
+                                        typename Pk<T>::P *e)
+{
+    using K = Pk<T>;
+    T v[VX + 2];
+    Io<S, T>::lds(r, v + 1);
+    v[0] = Io<S, T>::cvt_in(r[-1]);
+    v[VX + 1] = Io<S, T>::cvt_in(r[VX]);
+#pragma unroll
+    for (int p = 0; p < VX / 2; ++p) {
+        c[p] = K::mk(v[2 * p + 1], v[2 * p + 2]);
+        w[p] = K::mk(v[2 * p], v[2 * p + 1]);
+        e[p] = K::mk(v[2 * p + 2], v[2 * p + 3]);
+    }
+}
+
+// KIND: 0 = CF potential; 1..4 = TI global with exactly KIND coupling groups;
+// 5 = TI global with up to 13 groups (count read at run time)
 template <class S, class T, int STENCIL, int KIND, int TX, int TY>
 __device__ __forceinline__ void step_tile(const StepCoef<T> &C, const PackCoef<T> &PC,
-                                          const S *__restrict__ src, S *__restrict__ dst, int bx,
-                                          int by, int zc0, int zc1, T *__restrict__ sbuf)
+                                          const S *__restrict__ src, S *__restrict__ dst,
+                                          int *__restrict__ err, const CUtensorMap *tmap, int bx,
+                                          int by, int zc0, int zc1, S *__restrict__ stages,
+                                          uint64_t *full, uint64_t *empty)
 {
     using Sh = TileShape<S, T, TX, TY>;
     using K = Pk<T>;
     using P = typename K::P;
     constexpr int VX = Sh::VX, NP = Sh::NP, W = Sh::W, SW = Sh::SW, ROWS = Sh::ROWS;
-    constexpr int NTMAX = KIND == 1 ? 4 : kMaxTerms;
+    constexpr int STAGE = Sh::STAGE, NS = Sh::NS;
+    constexpr int NTMAX = KIND >= 1 && KIND <= 4 ? KIND : kMaxTerms;
 
     const GridGeom &g = C.g;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int tid = threadIdx.x;
     const int x0 = bx * W, y0 = by * TY;
+    const int nplanes = zc1 - zc0 + 2;   // planes zc0-1 .. zc1
+
+    if (tid >= Sh::NCONS) {
+        // ------------------------------------------------------- producer warp
+        if (tid != Sh::NCONS) return;
+        int issued = 0;
+        bool ok = true;
+        for (int i = 0; i < nplanes; ++i) {
+            const int s = i % NS;
+            if (i >= NS && !mbar_wait_sleep(&empty[s], ((i / NS) - 1) & 1)) { ok = false; break; }
+            if (tmap) {
+                mbar_expect_tx(&full[s], (uint32_t)Sh::BOX_BYTES);
+                // one box: padded x from the left halo chunk (x0), padded rows y0..,
+                // padded plane zc0 + i; out-of-range parts are zero-filled, never used
+                tma_load_3d(stages + s * STAGE, tmap, x0, y0, zc0 + i, &full[s]);
+            } else {
+                // row by row (no tensor map): the box's rows that lie in the buffer
+                const long long row0 = (long long)x0;
+                const int bytes_row = (int)min((long long)SW, (long long)g.pitch - row0) * (int)sizeof(S);
+                const int nrows = min(ROWS, g.ny + 2 - y0);
+                mbar_expect_tx(&full[s], (uint32_t)(bytes_row * nrows));
+                const S *plane = src + (long long)(zc0 + i) * g.plane + (long long)y0 * g.pitch + row0;
+                S *st = stages + s * STAGE;
+                for (int r = 0; r < nrows; ++r)
+                    bulk_g2s(st + r * SW, plane + (long long)r * g.pitch, (uint32_t)bytes_row, &full[s]);
+            }
+            ++issued;
+        }
+        if (!ok) atomicOr(err, 1);
+        // never leave with copies in flight
+        for (int i = max(0, issued - NS); i < issued; ++i)
+            if (!mbar_wait_sleep(&full[i % NS], (i / NS) & 1)) { atomicOr(err, 2); break; }
+        return;
+    }
+
+    // ------------------------------------------------------------- consumers
+    const int tx = tid % TX, ty = tid / TX;
+    const int lane = tid & 31;
     const int gx = x0 + tx * VX;
     const int gy = y0 + ty;
-    const bool has_extra = ty < 2;
-    const int extra_row = ty == 0 ? 0 : ROWS - 1;
-    const bool has_side = tid < 2 * ROWS;
-    const int side_row = tid >> 1, side_right = tid & 1;
     const bool out_ok = gy < g.ny && gx < g.nx;
+    const S *rbase = stages + (ty + 1) * SW + VX + tx * VX;   // own row in a stage
+    S *obase = dst + cell_index(g, gx, gy, 0);                // plane 0 of this column
 
-    // x/y ghost mapping of the three load slots, fixed for the whole march
-    const Slot s_own = make_slot(g, gx, gy, VX);
-    const Slot s_extra = has_extra ? make_slot(g, gx, ty == 0 ? y0 - 1 : y0 + TY, VX) : Slot{0, 0, -1, 0};
-    const Slot s_side = has_side ? make_slot(g, side_right ? x0 + W : x0 - 1, y0 + side_row - 1, 1)
-                                 : Slot{0, 0, -1, 0};
-    T *const own_dst0 = sbuf + (ty + 1) * SW + VX + tx * VX;
-    T *const extra_dst0 = sbuf + extra_row * SW + VX + tx * VX;
-    T *const side_dst0 = sbuf + side_row * SW + (side_right ? VX + W : VX - 1);
-
-    T own[VX], extra[VX], side[1];
-    auto fetch = [&](int z) {
-        int zf;
-        const int sz = map_axis(z, g.nz, g.bc[4], g.bc[5], &zf, 4);
-        const S *pb = src + (long long)sz * g.plane;
-        load_slot<S, T, VX>(C, pb, s_own, zf, own);
-        if (has_extra) load_slot<S, T, VX>(C, pb, s_extra, zf, extra);
-        if (has_side) load_slot<S, T, 1>(C, pb, s_side, zf, side);
-    };
-
-    S *out_base = dst + (long long)gy * g.pitch + gx;
-
-    // one arriving plane: publish, prefetch the next, reduce to plane quantities,
-    // and emit the output plane pz-1 from (m, z, p).  Returns false after the last.
-    auto body = [&](int k, PlaneQ<T, NP> &m, PlaneQ<T, NP> &z, PlaneQ<T, NP> &p) -> bool {
-        const int pz = zc0 - 1 + k;
-        const int boff = (k & 1) * (ROWS * SW);
-        put_row<T, VX>(own_dst0 + boff, own);
-        if (has_extra) put_row<T, VX>(extra_dst0 + boff, extra);
-        if (has_side) side_dst0[boff] = side[0];
-        if (pz < zc1) fetch(pz + 1);
-        __syncthreads();
-
+    auto body = [&](int i, PlaneQ<T, NP> &m, PlaneQ<T, NP> &z, PlaneQ<T, NP> &p) -> bool {
+        const int s = i % NS;
+        // warp-uniform: every lane waits (acquire), the warp goes on only if all saw it
+        if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (i / NS) & 1))) {
+            if (lane == 0) atomicOr(err, 4);
+            return false;
+        }
         {
-            const T *r0 = own_dst0 + boff;
-            RowPacks<T, VX> rc, rn, rs;
-            get_row<T, VX>(r0, rc);
-            get_row<T, VX>(r0 - SW, rn);
-            get_row<T, VX>(r0 + SW, rs);
+            const S *r0 = rbase + s * STAGE;
+            P cc[NP], cw[NP], ce[NP], nc[NP], nw[NP], ne[NP], sc[NP], sw[NP], se[NP];
+            get_row<S, T, VX>(r0, cc, cw, ce);
+            get_row<S, T, VX>(r0 - SW, nc, nw, ne);
+            get_row<S, T, VX>(r0 + SW, sc, sw, se);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
-                const P c = rc.c[q];
+                const P c = cc[q];
                 p.c[q] = c;
-                p.f[q] = K::add(K::add(K::sub(rc.w[q], c), K::sub(rc.e[q], c)),
-                                K::add(K::sub(rn.c[q], c), K::sub(rs.c[q], c)));
+                p.f[q] = K::add(K::add(K::sub(cw[q], c), K::sub(ce[q], c)),
+                                K::add(K::sub(nc[q], c), K::sub(sc[q], c)));
                 if (STENCIL != 6)
-                    p.e[q] = K::add(K::add(K::sub(rn.w[q], c), K::sub(rn.e[q], c)),
-                                    K::add(K::sub(rs.w[q], c), K::sub(rs.e[q], c)));
+                    p.e[q] = K::add(K::add(K::sub(nw[q], c), K::sub(ne[q], c)),
+                                    K::add(K::sub(sw[q], c), K::sub(se[q], c)));
             }
         }
-
-        if (k >= 2 && out_ok) {
+        if (i >= 2 && out_ok) {
             T outv[VX];
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
@@ -410,19 +400,19 @@ __device__ __forceinline__ void step_tile(const StepCoef<T> &C, const PackCoef<T
                     const P s3 = K::fma(PC.four, t, K::add(m.e[q], p.e[q]));
                     lap = K::fma(PC.c3, s3, lap);
                 }
-                const P s = K::fma(PC.m2, ph, PC.one);          // 1 - 2 phi
-                const P q1 = K::mul(ph, K::sub(PC.one, ph));     // phi (1 - phi)
-                const P qs = K::mul(q1, s);
+                const P sg = K::fma(PC.m2, ph, PC.one);          // 1 - 2 phi
+                const P q1 = K::mul(ph, K::sub(PC.one, ph));      // phi (1 - phi)
+                const P qs = K::mul(q1, sg);
                 P pot;
                 if (KIND == 0) {
                     pot = K::mul(PC.kappa, qs);
                 } else {
-                    const P u = K::mul(s, s);
+                    const P u = K::mul(sg, sg);
                     P num = PC.beta[0];
                     P den = K::fma(PC.nA[0], u, PC.one);
 #pragma unroll
                     for (int kk = 1; kk < NTMAX; ++kk) {
-                        if (kk < PC.nterms) {
+                        if (KIND <= 4 || kk < PC.nterms) {
                             const P d = K::fma(PC.nA[kk], u, PC.one);
                             num = K::fma(num, d, K::mul(PC.beta[kk], den));
                             den = K::mul(den, d);
@@ -433,10 +423,11 @@ __device__ __forceinline__ void step_tile(const StepCoef<T> &C, const PackCoef<T
                 P R = K::sub(lap, pot);
                 R = K::fma(PC.nkmu, q1, R);
                 const P o = K::fma(PC.dt, R, ph);
-                outv[pack_cell<VX>(q, 0)] = o.x;
-                outv[pack_cell<VX>(q, 1)] = o.y;
+                outv[2 * q] = o.x;
+                outv[2 * q + 1] = o.y;
             }
-            S *optr = out_base + (long long)(pz - 1) * g.plane;
+            const int oz = zc0 - 2 + i;   // output plane
+            S *optr = obase + (long long)oz * g.plane;
             if (gx + VX <= g.nx) {
                 Io<S, T>::st(optr, outv);
             } else {
@@ -445,31 +436,41 @@ __device__ __forceinline__ void step_tile(const StepCoef<T> &C, const PackCoef<T
                     if (gx + e < g.nx) optr[e] = Io<S, T>::cvt_out(outv[e]);
             }
         }
-        return pz < zc1;
+        return i + 1 < nplanes;
     };
 
     PlaneQ<T, NP> q0, q1, q2;
-    fetch(zc0 - 1);
-    for (int k = 0;; k += 3) {
-        if (!body(k, q1, q2, q0)) break;
-        if (!body(k + 1, q2, q0, q1)) break;
-        if (!body(k + 2, q0, q1, q2)) break;
+    for (int i = 0;; i += 3) {
+        if (!body(i, q1, q2, q0)) break;
+        if (!body(i + 1, q2, q0, q1)) break;
+        if (!body(i + 2, q0, q1, q2)) break;
     }
 }
 
-// minimum resident CTAs per SM: caps registers so three 256-thread CTAs fit
-template <class T> struct MinBlocks { static constexpr int value = sizeof(T) == 4 ? 3 : 2; };
+// minimum resident CTAs per SM (two 288-thread CTAs leave 113 registers a thread)
+template <class S> struct MinBlocks { static constexpr int value = SPFM_MIN_CTAS; };
 
 template <class S, class T, int STENCIL, int KIND, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY, MinBlocks<T>::value)
+__global__ void __launch_bounds__(TileShape<S, T, TX, TY>::NTHREADS, MinBlocks<S>::value)
     spfm_step_kernel(const StepCoef<T> C, const PackCoef<T> PC, const S *__restrict__ src,
-                     S *__restrict__ dst, int zchunk)
+                     S *__restrict__ dst, int *__restrict__ err, int zchunk,
+                     const __grid_constant__ CUtensorMap tmap, int use_tmap)
 {
     using Sh = TileShape<S, T, TX, TY>;
-    __shared__ __align__(16) T sbuf[Sh::SMEM_ELEMS];
+    __shared__ __align__(128) S stages[Sh::NS * Sh::STAGE];
+    __shared__ __align__(8) uint64_t full[Sh::NS], empty[Sh::NS];
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < Sh::NS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], Sh::NCONS / 32);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
     const int zc0 = blockIdx.z * zchunk;
     const int zc1 = min(zc0 + zchunk, C.g.nz);
-    step_tile<S, T, STENCIL, KIND, TX, TY>(C, PC, src, dst, blockIdx.x, blockIdx.y, zc0, zc1, sbuf);
+    step_tile<S, T, STENCIL, KIND, TX, TY>(C, PC, src, dst, err, use_tmap ? &tmap : nullptr,
+                                           blockIdx.x, blockIdx.y, zc0, zc1, stages, full, empty);
 }
 
 // z-chunk length so that the launch has enough CTAs for 152 SMs
@@ -484,22 +485,32 @@ inline int pick_zchunk(int tiles_xy, int nz)
 }
 
 template <class S, class T, int TX, int TY>
-cudaError_t launch_step_t(const StepCoef<T> &c, const S *src, S *dst, LaunchCfg cfg, cudaStream_t st)
+cudaError_t launch_step_t(const StepCoef<T> &c, const S *src, S *dst, int *err, LaunchCfg cfg,
+                          const CUtensorMap *tmap, cudaStream_t st)
 {
     using Sh = TileShape<S, T, TX, TY>;
-    const dim3 block(TX, TY);
     const int gxn = (c.g.nx + Sh::W - 1) / Sh::W, gyn = (c.g.ny + TY - 1) / TY;
     const int zchunk = pick_zchunk(gxn * gyn, c.g.nz);
     const dim3 grid(gxn, gyn, (c.g.nz + zchunk - 1) / zchunk);
-    const int kind = cfg.scheme == SPFM_FD ? 0 : (c.nterms <= 4 ? 1 : 2);
+    // exact group counts 1..4 get their own kernels; 0 groups (all A_k = 0)
+    // runs the one-group kernel with beta = 0
+    const int kind = cfg.scheme == SPFM_FD ? 0 : (c.nterms <= 4 ? (c.nterms < 1 ? 1 : c.nterms) : 5);
     const PackCoef<T> pc = make_pack_coef<T>(c);
-#define SPFM_LAUNCH(ST, KD) \
-    spfm_step_kernel<S, T, ST, KD, TX, TY><<<grid, block, 0, st>>>(c, pc, src, dst, zchunk)
+    CUtensorMap map;
+    if (tmap) map = *tmap;
+    else memset(&map, 0, sizeof map);
+    const int use = tmap ? 1 : 0;
+#define SPFM_LAUNCH(ST, KD)                                                                   \
+    spfm_step_kernel<S, T, ST, KD, TX, TY><<<grid, Sh::NTHREADS, 0, st>>>(c, pc, src, dst, err, \
+                                                                          zchunk, map, use)
 #define SPFM_BY_KIND(ST)                        \
     do {                                        \
         if (kind == 0) SPFM_LAUNCH(ST, 0);      \
         else if (kind == 1) SPFM_LAUNCH(ST, 1); \
-        else SPFM_LAUNCH(ST, 2);                \
+        else if (kind == 2) SPFM_LAUNCH(ST, 2); \
+        else if (kind == 3) SPFM_LAUNCH(ST, 3); \
+        else if (kind == 4) SPFM_LAUNCH(ST, 4); \
+        else SPFM_LAUNCH(ST, 5);                \
     } while (0)
     if (cfg.stencil == 6) SPFM_BY_KIND(6);
     else if (cfg.stencil == 18) SPFM_BY_KIND(18);

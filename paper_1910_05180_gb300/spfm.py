@@ -18,7 +18,8 @@ import threading
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libspfm_gb300.so")
+# SPFM_LIBRARY may point at another build of the same library (same ABI)
+LIB_PATH = os.environ.get("SPFM_LIBRARY") or os.path.join(HERE, "_build", "libspfm_gb300.so")
 
 SPFM_OK, SPFM_EINVAL, SPFM_EUNSTABLE, SPFM_EPHASE = 0, -1, -2, -3
 SPFM_ECUDA, SPFM_ENONFINITE, SPFM_ETIMEOUT, SPFM_ENOMEM = -4, -5, -6, -7
@@ -78,7 +79,8 @@ _D = ctypes.c_double
 _I = ctypes.c_int
 SIGNATURES = [
     ("spfm_layout", _I, [ctypes.POINTER(GridDesc), ctypes.POINTER(ctypes.c_size_t),
-                         ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+                         ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
+                         ctypes.POINTER(ctypes.c_size_t)]),
     ("spfm_create_grid", _I, [ctypes.POINTER(GridDesc), ctypes.POINTER(_P)]),
     ("spfm_destroy_grid", _I, [_P]),
     ("spfm_set_stream", _I, [_P, _P]),
@@ -125,9 +127,11 @@ def _check(status: int, handle=None):
 # ------------------------------------------------------------- C-named calls
 
 def spfm_layout(desc: GridDesc):
-    px, fb, sb = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
-    _check(load().spfm_layout(ctypes.byref(desc), ctypes.byref(px), ctypes.byref(fb), ctypes.byref(sb)))
-    return px.value, fb.value, sb.value
+    """(pitch_x, x_off, field_bytes, scratch_bytes) of a grid."""
+    px, xo, fb, sb = (ctypes.c_size_t() for _ in range(4))
+    _check(load().spfm_layout(ctypes.byref(desc), ctypes.byref(px), ctypes.byref(xo),
+                              ctypes.byref(fb), ctypes.byref(sb)))
+    return px.value, xo.value, fb.value, sb.value
 
 
 def spfm_create_grid(desc: GridDesc):
@@ -197,11 +201,12 @@ class Grid:
         for i in range(3):
             d.n[i], d.gamma[i], d.center[i] = float(n[i]), float(gamma[i]), float(center[i])
         d.C_gamma = float(C_gamma)
-        pitch, fbytes, sbytes = spfm_layout(d)
-        self.pitch, self.field_bytes, self.scratch_bytes = pitch, fbytes, sbytes
+        pitch, xoff, fbytes, sbytes = spfm_layout(d)
+        self.pitch, self.x_off, self.field_bytes, self.scratch_bytes = pitch, xoff, fbytes, sbytes
         tdt = TORCH_DTYPE[dtype]
         self.shape = (int(nz), int(ny), int(nx))
-        self.fields = [torch.zeros((nz, ny, pitch), dtype=tdt, device=device) for _ in range(2)]
+        # ghosted buffers: (nz + 2, ny + 2, pitch), interior at [1:-1, 1:-1, x_off:x_off+nx]
+        self.fields = [torch.zeros((nz + 2, ny + 2, pitch), dtype=tdt, device=device) for _ in range(2)]
         self.scratch = torch.empty(max(sbytes, 16), dtype=torch.uint8, device=device)
         for b in range(2):
             d.field[b] = self.fields[b].data_ptr()
@@ -240,8 +245,14 @@ class Grid:
         return spfm_interface_stats(self.handle, flags, allow_nonfinite)
 
     def current(self) -> torch.Tensor:
-        """View (nz, ny, nx) of the device buffer holding the current field."""
-        return self.fields[spfm_current(self.handle)][..., : self.shape[2]]
+        """View (nz, ny, nx) of the interior of the buffer holding the current field."""
+        buf = self.fields[spfm_current(self.handle)]
+        return buf[1:-1, 1:-1, self.x_off: self.x_off + self.shape[2]]
+
+    def current_with_ghosts(self) -> torch.Tensor:
+        """View (nz+2, ny+2, nx+2) of the current buffer including the ghost layer."""
+        buf = self.fields[spfm_current(self.handle)]
+        return buf[:, :, self.x_off - 1: self.x_off + self.shape[2] + 1]
 
     def get_field(self, to_host=True) -> torch.Tensor:
         """Dense copy of the current field through spfm_get_field."""

@@ -56,17 +56,17 @@ def _desc(nx=10, ny=7, nz=5, dtype=S.SPFM_F32, bc=(S.SPFM_PERIODIC,) * 6, n=(1.0
 @pytest.mark.parametrize("dtype,per16", [(S.SPFM_F64, 2), (S.SPFM_F32, 4), (S.SPFM_BF16, 8)])
 def test_layout_pitch_is_16_byte_rows(lib, dtype, per16):
     for nx in (1, 3, 4, 17, 128, 130):
-        px, fb, sb = S.spfm_layout(_desc(nx=nx, dtype=dtype))
-        assert px % per16 == 0 and nx <= px < nx + per16
+        px, xo, fb, sb = S.spfm_layout(_desc(nx=nx, dtype=dtype))
+        assert xo == per16 and px % per16 == 0 and xo + nx + 1 <= px < xo + nx + 1 + per16
         es = {S.SPFM_F64: 8, S.SPFM_F32: 4, S.SPFM_BF16: 2}[dtype]
-        assert fb == px * 7 * 5 * es
+        assert fb == px * (7 + 2) * (5 + 2) * es
         assert sb > 0
 
 
 def _fake_grid(lib, **kw):
     """A handle over fake, aligned pointers: fine for calls that fail validation."""
     d = _desc(**kw)
-    _, _, sb = S.spfm_layout(d)
+    _, _, _, sb = S.spfm_layout(d)
     d.field[0], d.field[1] = 0x10000, 0x20000
     d.scratch, d.scratch_bytes = 0x30000, sb
     return S.spfm_create_grid(d)

@@ -133,7 +133,10 @@ def test_stats_and_energy_match_oracle(dtype):
     for k in ("volume", "S_w", "S_c", "phi_min", "phi_max", "position"):
         assert abs(st[k] - ref[k]) <= 1e-12 * max(1.0, abs(ref[k])), (k, st[k], ref[k])
     e_ref = O.energy(p, start)
-    assert abs(st["energy"] - e_ref) <= 1e-12 * abs(e_ref)
+    # an FP32 grid stores its contact-angle ghost cells in FP32 (the oracle's are
+    # FP64), and the forward differences of Eq. 1 read them
+    e_tol = 1e-12 if dtype == S.SPFM_F64 else 1e-8
+    assert abs(st["energy"] - e_ref) <= e_tol * abs(e_ref)
     # radius estimator on a sphere
     ctr = (24.5, 19.5, 14.5)
     g.init_sphere(ctr, 9.0, 2.0)
