@@ -180,7 +180,7 @@ int build_model(spfm_grid *g, double M, double Gamma, double lambda, double dx, 
 }
 
 template <class T>
-void fill_coef(const spfm_grid *g, const Model &m, double dt, StepCoef<T> &c)
+void fill_coef(const spfm_grid *g, const Model &m, double dt, int stencil, StepCoef<T> &c)
 {
     memset(&c, 0, sizeof c);
     c.g = g->geom;
@@ -196,7 +196,18 @@ void fill_coef(const spfm_grid *g, const Model &m, double dt, StepCoef<T> &c)
         c.beta[t] = t < m.nterms ? (T)m.beta[t] : T(0);
         c.A[t] = t < m.nterms ? (T)m.A[t] : T(0);
         c.ck[t] = (T)m.ck[t];
+        c.nbetadt[t] = t < m.nterms ? (T)(-m.beta[t] * dt) : T(0);
     }
+    // S1 = F'_z + t, S2 = E'_z + F'_{z-1} + F'_{z+1} + 4t, S3 = E'_{z-1} + E'_{z+1} + 4t
+    double ct = m.c_shell[0];
+    if (stencil >= 18) ct += 4.0 * m.c_shell[1];
+    if (stencil == 26) ct += 4.0 * m.c_shell[2];
+    c.c1dt = (T)(m.c_shell[0] * dt);
+    c.c2dt = (T)(m.c_shell[1] * dt);
+    c.c3dt = (T)(m.c_shell[2] * dt);
+    c.ctdt = (T)(ct * dt);
+    c.nkmudt = (T)(-m.kmu * dt);
+    c.nkapdt = (T)(-m.kappa * dt);
 }
 
 cudaStream_t stream_of(const spfm_grid *g) { return (cudaStream_t)g->d.stream; }
@@ -236,6 +247,9 @@ spfm_status spfm_create_grid(const spfm_grid_desc *d, spfm_grid **out)
     size_t px = 0, off = 0, fb = 0, sb = 0;
     spfm_status st = spfm_layout(d, &px, &off, &fb, &sb);
     if (st != SPFM_OK) return st;
+    if ((long long)(d->nx + 2) * (d->ny + 2) >= (1LL << 30) || (long long)(d->nx + 2) * d->nz >= (1LL << 30) ||
+        (long long)d->ny * d->nz >= (1LL << 30))
+        return fail(nullptr, SPFM_EINVAL, "spfm_create_grid: a face of the grid exceeds 2^30 cells");
     if ((long long)px * (d->ny + 2) * (long long)(d->nz + 2) >= (1LL << 40))
         return fail(nullptr, SPFM_EINVAL, "spfm_create_grid: grid too large");
     for (int f = 0; f < 6; ++f)
@@ -295,7 +309,7 @@ static spfm_status refresh_ghosts(spfm_grid *g, double lambda, double dx)
         const double sgn = (f % 2 == 0) ? -1.0 : 1.0;
         af[f] = tanh(2.0 * sgn * dx * g->d.n[f / 2] / lambda);
     }
-    cudaError_t e = launch_fill_ghosts(g->geom, g->d.dtype, af, g->d.field[g->cur], stream_of(g));
+    cudaError_t e = launch_fill_ghosts(g->geom, g->d.dtype, af, g->d.field[g->cur], stream_of(g), 1);
     if (e != cudaSuccess) return cuda_fail(g, e, "ghost fill");
     g->ghosts_dirty = false;
     g->ghost_lambda = lambda;
@@ -367,19 +381,19 @@ spfm_status spfm_step(spfm_grid *g, int n_steps, double M, double Gamma, double 
     int *err = err_word(g);
     if (g->d.dtype == SPFM_F64) {
         StepCoef<double> c;
-        fill_coef<double>(g, m, dt, c);
+        fill_coef<double>(g, m, dt, stencil, c);
         for (int i = 0; i < n_steps; ++i) {
             cudaError_t e = launch_step_f64(c, (const double *)g->d.field[g->cur],
                                             (double *)g->d.field[1 - g->cur], err, cfg, &g->tma,
                                             g->cur, s);
             if (e == cudaSuccess)
-                e = launch_fill_ghosts(g->geom, g->d.dtype, m.aface, g->d.field[1 - g->cur], s);
+                e = launch_fill_ghosts(g->geom, g->d.dtype, m.aface, g->d.field[1 - g->cur], s, 1);
             if (e != cudaSuccess) return cuda_fail(g, e, "spfm_step");
             g->cur ^= 1;
         }
     } else {
         StepCoef<float> c;
-        fill_coef<float>(g, m, dt, c);
+        fill_coef<float>(g, m, dt, stencil, c);
         for (int i = 0; i < n_steps; ++i) {
             cudaError_t e;
             if (g->d.dtype == SPFM_F32)
@@ -390,7 +404,7 @@ spfm_status spfm_step(spfm_grid *g, int n_steps, double M, double Gamma, double 
                                      (__nv_bfloat16 *)g->d.field[1 - g->cur], err, cfg, &g->tma,
                                      g->cur, s);
             if (e == cudaSuccess)
-                e = launch_fill_ghosts(g->geom, g->d.dtype, m.aface, g->d.field[1 - g->cur], s);
+                e = launch_fill_ghosts(g->geom, g->d.dtype, m.aface, g->d.field[1 - g->cur], s, 1);
             if (e != cudaSuccess) return cuda_fail(g, e, "spfm_step");
             g->cur ^= 1;
         }

@@ -12,7 +12,7 @@
 //   z faces  k in {-1, nz}, all (i, j) in [-1, nx] x [-1, ny]
 //   y faces  j in {-1, ny}, (i, k) in [-1, nx] x [0, nz)
 //   x faces  i in {-1, nx}, (j, k) in [0, ny) x [0, nz)
-// One launch after every step (arithmetic in the step kernels' compute type).
+// Arithmetic in the step kernels' compute type.
 #include "spfm_internal.h"
 
 namespace spfm {
@@ -30,6 +30,7 @@ struct FaceArgs {
     GridGeom g;
     double aface[6];
     long long nzf, nyf, nxf;   // ghost counts of the z, y and x faces (both sides)
+    int zper, yper, xper;      // ghost cells per side of each face
 };
 
 template <class S>
@@ -42,23 +43,20 @@ __global__ void __launch_bounds__(256) ghost_kernel(const FaceArgs a, S *f)
          t += (long long)gridDim.x * blockDim.x) {
         int i, j, k;
         if (t < a.nzf) {
-            const long long per = (long long)(g.nx + 2) * (g.ny + 2);
-            const long long r = t % per;
-            k = t < per ? -1 : g.nz;
-            j = (int)(r / (g.nx + 2)) - 1;
-            i = (int)(r % (g.nx + 2)) - 1;
+            const int u = (int)t, side = u >= a.zper, r = u - side * a.zper;
+            k = side ? g.nz : -1;
+            j = r / (g.nx + 2) - 1;
+            i = r - (j + 1) * (g.nx + 2) - 1;
         } else if (t < a.nzf + a.nyf) {
-            const long long u = t - a.nzf, per = (long long)(g.nx + 2) * g.nz;
-            const long long r = u % per;
-            j = u < per ? -1 : g.ny;
-            k = (int)(r / (g.nx + 2));
-            i = (int)(r % (g.nx + 2)) - 1;
+            const int u = (int)(t - a.nzf), side = u >= a.yper, r = u - side * a.yper;
+            j = side ? g.ny : -1;
+            k = r / (g.nx + 2);
+            i = r - k * (g.nx + 2) - 1;
         } else {
-            const long long u = t - a.nzf - a.nyf, per = (long long)g.ny * g.nz;
-            const long long r = u % per;
-            i = u < per ? -1 : g.nx;
-            k = (int)(r / g.ny);
-            j = (int)(r % g.ny);
+            const int u = (int)(t - a.nzf - a.nyf), side = u >= a.xper, r = u - side * a.xper;
+            i = side ? g.nx : -1;
+            k = r / g.ny;
+            j = r - k * g.ny;
         }
         int fx, fy, fz;
         const int sx = map_axis(i, g.nx, g.bc[0], g.bc[1], &fx, 0);
@@ -73,14 +71,17 @@ __global__ void __launch_bounds__(256) ghost_kernel(const FaceArgs a, S *f)
 }
 
 cudaError_t launch_fill_ghosts(const GridGeom &g, int dtype, const double aface[6], void *field,
-                               cudaStream_t st)
+                               cudaStream_t st, int x_faces)
 {
     FaceArgs a;
     a.g = g;
     for (int f = 0; f < 6; ++f) a.aface[f] = aface[f];
-    a.nzf = 2LL * (g.nx + 2) * (g.ny + 2);
-    a.nyf = 2LL * (g.nx + 2) * g.nz;
-    a.nxf = 2LL * g.ny * g.nz;
+    a.zper = (g.nx + 2) * (g.ny + 2);
+    a.yper = (g.nx + 2) * g.nz;
+    a.xper = g.ny * g.nz;
+    a.nzf = 2LL * a.zper;
+    a.nyf = 2LL * a.yper;
+    a.nxf = x_faces ? 2LL * a.xper : 0;
     const long long total = a.nzf + a.nyf + a.nxf;
     long long blocks = (total + 255) / 256;
     if (blocks > 2 * 152 * 8) blocks = 2 * 152 * 8;

@@ -69,6 +69,11 @@ struct StepCoef {
     int nterms;             // TI: distinct non-zero A_k after grouping
     T beta[kMaxTerms];      // TI: summed 4 c_k A_k of each group
     T A[kMaxTerms];         // TI: the group's A_k = a_k^2
+    // the same coefficients multiplied by dt in FP64 before rounding (the step
+    // kernels fold the Euler update into them): c_j dt, the weight of
+    // t = (phi_{z-1} - phi) + (phi_{z+1} - phi), -beta dt, -kmu dt, -kappa dt
+    T c1dt, c2dt, c3dt, ctdt, nkmudt, nkapdt;
+    T nbetadt[kMaxTerms];
     // TI_n (local normal): per-direction c_k, (lambda/2), 1/(2 dx), 2 dx/lambda, clamp
     T ck[kMaxTerms];
     T half_lam, inv_2dx, two_dx_over_lam, eps;
@@ -146,9 +151,10 @@ struct InitArgs {
 };
 cudaError_t launch_init(const InitArgs &a, void *field, cudaStream_t st);
 
-// Ghost layer of a whole buffer from its interior (after init / set_field).
+// Ghost layer of a buffer from its interior: all faces (x_faces = 1) or the y
+// and z faces only.  Face sizes must stay below 2^31 cells.
 cudaError_t launch_fill_ghosts(const GridGeom &g, int dtype, const double aface[6], void *field,
-                               cudaStream_t st);
+                               cudaStream_t st, int x_faces);
 
 struct StatsArgs {
     GridGeom g;

@@ -12,8 +12,8 @@
 // wait is bounded: on timeout the thread sets the error word and leaves.
 //
 // Boundary conditions.  The kernel reads the ghost layer and writes interior
-// cells only; a separate face kernel (boundary.cu) refreshes the ghosts of the
-// new field after each step, so the hot path holds no boundary logic.
+// cells only; a face kernel (boundary.cu) refreshes the ghosts of the new
+// field after each step, so the hot path holds no boundary logic.
 //
 // Arithmetic.  From each plane every thread forms, for its cells,
 //   C  = phi at the cell,
@@ -38,10 +38,10 @@ namespace spfm {
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz per bounded wait
 
 #ifndef SPFM_STAGES
-#define SPFM_STAGES 4         // planes in flight per CTA
+#define SPFM_STAGES 6         // planes in flight per CTA
 #endif
 #ifndef SPFM_MIN_CTAS
-#define SPFM_MIN_CTAS 2       // resident CTAs per SM the register budget is sized for
+#define SPFM_MIN_CTAS 3       // resident CTAs per SM the register budget is sized for
 #endif
 
 // ------------------------------------------------------------ pack arithmetic
@@ -55,9 +55,14 @@ template <> struct Pk<float> {
     static __device__ __forceinline__ P mul(P a, P b) { return __fmul2_rn(a, b); }
     static __device__ __forceinline__ P fma(P a, P b, P c) { return __ffma2_rn(a, b, c); }
     static __device__ __forceinline__ P sub(P a, P b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+    // a / b as a * rcp(b): two MUFU reciprocals (|rel. error| < 2^-22) and one
+    // packed multiply, the accuracy of __fdividef without splitting the pack
     static __device__ __forceinline__ P div(P a, P b)
     {
-        return make_float2(__fdividef(a.x, b.x), __fdividef(a.y, b.y));
+        float2 r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(b.x));
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(b.y));
+        return __fmul2_rn(a, r);
     }
 };
 
@@ -80,12 +85,15 @@ template <class T> struct PackT;
 template <> struct PackT<float> { using P = float2; static P splat(float v) { return make_float2(v, v); } };
 template <> struct PackT<double> { using P = D2; static P splat(double v) { return {v, v}; } };
 
-// Step coefficients pre-splatted into packs (kernel parameter space).
+// Step coefficients pre-splatted into packs (kernel parameter space), with dt
+// folded in: phi' = phi + c1 dt S1' + c2 dt S2' + c3 dt S3'
+//                 + q (s sum_k (-beta_k dt)/(1 - A_k s^2) - kmu dt)      (TI)
+//                 + q (s (-kappa dt) - kmu dt)                          (CF)
 template <class T>
 struct PackCoef {
     using P = typename PackT<T>::P;
-    P one, m2, four, c1, c2, c3, dt, nkmu, kappa;
-    P nA[kMaxTerms], beta[kMaxTerms];
+    P one, m2, m4, c1, c2, c3, ct, nkmu, nkap;
+    P nA[kMaxTerms], nbeta[kMaxTerms];
     int nterms;
 };
 
@@ -96,16 +104,16 @@ inline PackCoef<T> make_pack_coef(const StepCoef<T> &c)
     PackCoef<T> p;
     p.one = PT::splat(T(1));
     p.m2 = PT::splat(T(-2));
-    p.four = PT::splat(T(4));
-    p.c1 = PT::splat(c.c1);
-    p.c2 = PT::splat(c.c2);
-    p.c3 = PT::splat(c.c3);
-    p.dt = PT::splat(c.dt);
-    p.nkmu = PT::splat(-c.kmu);
-    p.kappa = PT::splat(c.kappa);
+    p.m4 = PT::splat(T(-4));
+    p.c1 = PT::splat(c.c1dt);
+    p.c2 = PT::splat(c.c2dt);
+    p.c3 = PT::splat(c.c3dt);
+    p.ct = PT::splat(c.ctdt);
+    p.nkmu = PT::splat(c.nkmudt);
+    p.nkap = PT::splat(c.nkapdt);
     for (int k = 0; k < kMaxTerms; ++k) {
         p.nA[k] = PT::splat(-c.A[k]);
-        p.beta[k] = PT::splat(c.beta[k]);
+        p.nbeta[k] = PT::splat(c.nbetadt[k]);
     }
     p.nterms = c.nterms;
     return p;
@@ -257,24 +265,31 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
 
 // -------------------------------------------------------------------- tile
 
+#ifndef SPFM_ROWS_PER_THREAD
+#define SPFM_ROWS_PER_THREAD 2
+#endif
+
 template <class S, class T, int TX, int TY>
 struct TileShape {
     static constexpr int VX = Io<S, T>::VX;
     static constexpr int NP = VX / 2;
+    static constexpr int RPT = SPFM_ROWS_PER_THREAD;   // rows of the tile per consumer thread
     static constexpr int W = TX * VX;
     static constexpr int SW = W + 2 * VX;   // staged row: one 16-byte chunk of halo per side
     static constexpr int ROWS = TY + 2;
     static constexpr int BOX_BYTES = ROWS * SW * (int)sizeof(S);          // one TMA box
     static constexpr int STAGE = ((BOX_BYTES + 127) / 128 * 128) / (int)sizeof(S);   // 128-B aligned
     static constexpr int NS = SPFM_STAGES;  // pipeline depth (planes)
-    static constexpr int NCONS = TX * TY;   // consumer threads
+    static constexpr int NCONS = TX * TY / RPT;   // consumer threads
     static constexpr int NTHREADS = NCONS + 32;
 };
 
+// Per plane and pack: c = phi, h = c1 dt F' + c2 dt E' (the plane as the centre
+// plane of an output), g = c2 dt F' + c3 dt E' (as the plane above or below).
 template <class T, int NP>
 struct PlaneQ {
     using P = typename Pk<T>::P;
-    P c[NP], f[NP], e[NP];
+    P c[NP], h[NP], g[NP];
 };
 
 // The packs of one staged row around a thread's cells (adjacent pairs):
@@ -351,15 +366,16 @@ __device__ __forceinline__ void step_tile(const StepCoef<T> &C, const PackCoef<T
     }
 
     // ------------------------------------------------------------- consumers
-    const int tx = tid % TX, ty = tid / TX;
+    constexpr int RPT = Sh::RPT;
+    const int tx = tid % TX, ty = (tid / TX) * RPT;   // first of the thread's RPT rows
     const int lane = tid & 31;
     const int gx = x0 + tx * VX;
     const int gy = y0 + ty;
-    const bool out_ok = gy < g.ny && gx < g.nx;
-    const S *rbase = stages + (ty + 1) * SW + VX + tx * VX;   // own row in a stage
-    S *obase = dst + cell_index(g, gx, gy, 0);                // plane 0 of this column
+    const S *rbase = stages + (ty + 1) * SW + VX + tx * VX;   // first own row in a stage
+    S *obase = dst + cell_index(g, gx, gy, 0);                // plane 0, first own row
 
-    auto body = [&](int i, PlaneQ<T, NP> &m, PlaneQ<T, NP> &z, PlaneQ<T, NP> &p) -> bool {
+    auto body = [&](int i, PlaneQ<T, NP> (&m)[RPT], PlaneQ<T, NP> (&z)[RPT],
+                    PlaneQ<T, NP> (&p)[RPT]) -> bool {
         const int s = i % NS;
         // warp-uniform: every lane waits (acquire), the warp goes on only if all saw it
         if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (i / NS) & 1))) {
@@ -367,79 +383,82 @@ __device__ __forceinline__ void step_tile(const StepCoef<T> &C, const PackCoef<T
             return false;
         }
         {
-            const S *r0 = rbase + s * STAGE;
-            P cc[NP], cw[NP], ce[NP], nc[NP], nw[NP], ne[NP], sc[NP], sw[NP], se[NP];
-            get_row<S, T, VX>(r0, cc, cw, ce);
-            get_row<S, T, VX>(r0 - SW, nc, nw, ne);
-            get_row<S, T, VX>(r0 + SW, sc, sw, se);
+            // rows ty-1 .. ty+RPT of the stage (north halo, own rows, south halo)
+            const S *r0 = rbase + s * STAGE - SW;
+            P rc[RPT + 2][NP], rw[RPT + 2][NP], re[RPT + 2][NP];
+#pragma unroll
+            for (int r = 0; r < RPT + 2; ++r) get_row<S, T, VX>(r0 + r * SW, rc[r], rw[r], re[r]);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
 #pragma unroll
-            for (int q = 0; q < NP; ++q) {
-                const P c = cc[q];
-                p.c[q] = c;
-                p.f[q] = K::add(K::add(K::sub(cw[q], c), K::sub(ce[q], c)),
-                                K::add(K::sub(nc[q], c), K::sub(sc[q], c)));
-                if (STENCIL != 6)
-                    p.e[q] = K::add(K::add(K::sub(nw[q], c), K::sub(ne[q], c)),
-                                    K::add(K::sub(sw[q], c), K::sub(se[q], c)));
+            for (int r = 0; r < RPT; ++r) {
+#pragma unroll
+                for (int q = 0; q < NP; ++q) {
+                    const P c = rc[r + 1][q];
+                    p[r].c[q] = c;
+                    // F' = (W + E + N + S) - 4C, E' = (NW + NE + SW + SE) - 4C
+                    const P f = K::fma(PC.m4, c, K::add(K::add(rw[r + 1][q], re[r + 1][q]),
+                                                        K::add(rc[r][q], rc[r + 2][q])));
+                    if (STENCIL == 6) {
+                        p[r].h[q] = K::mul(PC.c1, f);
+                    } else {
+                        const P e = K::fma(PC.m4, c, K::add(K::add(rw[r][q], re[r][q]),
+                                                            K::add(rw[r + 2][q], re[r + 2][q])));
+                        p[r].h[q] = K::fma(PC.c2, e, K::mul(PC.c1, f));
+                        p[r].g[q] = STENCIL == 26 ? K::fma(PC.c3, e, K::mul(PC.c2, f)) : K::mul(PC.c2, f);
+                    }
+                }
             }
         }
-        if (i >= 2 && out_ok) {
-            T outv[VX];
-#pragma unroll
-            for (int q = 0; q < NP; ++q) {
-                const P ph = z.c[q];
-                const P t = K::add(K::sub(m.c[q], ph), K::sub(p.c[q], ph));
-                P lap = K::mul(PC.c1, K::add(z.f[q], t));
-                if (STENCIL != 6) {
-                    const P s2 = K::fma(PC.four, t, K::add(z.e[q], K::add(m.f[q], p.f[q])));
-                    lap = K::fma(PC.c2, s2, lap);
-                }
-                if (STENCIL == 26) {
-                    const P s3 = K::fma(PC.four, t, K::add(m.e[q], p.e[q]));
-                    lap = K::fma(PC.c3, s3, lap);
-                }
-                const P sg = K::fma(PC.m2, ph, PC.one);          // 1 - 2 phi
-                const P q1 = K::mul(ph, K::sub(PC.one, ph));      // phi (1 - phi)
-                const P qs = K::mul(q1, sg);
-                P pot;
-                if (KIND == 0) {
-                    pot = K::mul(PC.kappa, qs);
-                } else {
-                    const P u = K::mul(sg, sg);
-                    P num = PC.beta[0];
-                    P den = K::fma(PC.nA[0], u, PC.one);
-#pragma unroll
-                    for (int kk = 1; kk < NTMAX; ++kk) {
-                        if (KIND <= 4 || kk < PC.nterms) {
-                            const P d = K::fma(PC.nA[kk], u, PC.one);
-                            num = K::fma(num, d, K::mul(PC.beta[kk], den));
-                            den = K::mul(den, d);
-                        }
-                    }
-                    pot = K::mul(qs, K::div(num, den));
-                }
-                P R = K::sub(lap, pot);
-                R = K::fma(PC.nkmu, q1, R);
-                const P o = K::fma(PC.dt, R, ph);
-                outv[2 * q] = o.x;
-                outv[2 * q + 1] = o.y;
-            }
+        if (i >= 2) {
             const int oz = zc0 - 2 + i;   // output plane
-            S *optr = obase + (long long)oz * g.plane;
-            if (gx + VX <= g.nx) {
-                Io<S, T>::st(optr, outv);
-            } else {
 #pragma unroll
-                for (int e = 0; e < VX; ++e)
-                    if (gx + e < g.nx) optr[e] = Io<S, T>::cvt_out(outv[e]);
+            for (int r = 0; r < RPT; ++r) {
+                if (gy + r >= g.ny || gx >= g.nx) continue;
+                T outv[VX];
+#pragma unroll
+                for (int q = 0; q < NP; ++q) {
+                    const P ph = z[r].c[q];
+                    const P t = K::add(K::sub(m[r].c[q], ph), K::sub(p[r].c[q], ph));
+                    P acc = K::add(K::fma(PC.ct, t, ph), z[r].h[q]);      // phi + dt * Laplacian
+                    if (STENCIL != 6) acc = K::add(acc, K::add(m[r].g[q], p[r].g[q]));
+                    const P sg = K::fma(PC.m2, ph, PC.one);               // s = 1 - 2 phi
+                    const P q1 = K::mul(ph, K::sub(PC.one, ph));          // q = phi (1 - phi)
+                    P w;   // -dt (potential / q + 4 M dF / (lambda Gamma))
+                    if (KIND == 0) {
+                        w = K::fma(sg, PC.nkap, PC.nkmu);
+                    } else {
+                        const P u = K::mul(sg, sg);
+                        P num = PC.nbeta[0];
+                        P den = K::fma(PC.nA[0], u, PC.one);
+#pragma unroll
+                        for (int kk = 1; kk < NTMAX; ++kk) {
+                            if (KIND <= 4 || kk < PC.nterms) {
+                                const P d = K::fma(PC.nA[kk], u, PC.one);
+                                num = K::fma(num, d, K::mul(PC.nbeta[kk], den));
+                                den = K::mul(den, d);
+                            }
+                        }
+                        w = K::fma(sg, K::div(num, den), PC.nkmu);
+                    }
+                    const P o = K::fma(q1, w, acc);
+                    outv[2 * q] = o.x;
+                    outv[2 * q + 1] = o.y;
+                }
+                S *optr = obase + (long long)oz * g.plane + (long long)r * g.pitch;
+                if (gx + VX <= g.nx) {
+                    Io<S, T>::st(optr, outv);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < VX; ++e)
+                        if (gx + e < g.nx) optr[e] = Io<S, T>::cvt_out(outv[e]);
+                }
             }
         }
         return i + 1 < nplanes;
     };
 
-    PlaneQ<T, NP> q0, q1, q2;
+    PlaneQ<T, NP> q0[RPT], q1[RPT], q2[RPT];
     for (int i = 0;; i += 3) {
         if (!body(i, q1, q2, q0)) break;
         if (!body(i + 1, q2, q0, q1)) break;
