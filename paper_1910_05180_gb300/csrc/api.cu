@@ -9,7 +9,7 @@
 #include <string>
 #include <vector>
 
-#include "spfm_internal.h"
+#include "host_internal.h"
 
 using namespace spfm;
 
@@ -19,23 +19,9 @@ thread_local std::string t_err;
 
 }  // namespace
 
-struct spfm_grid {
-    spfm_grid_desc d;
-    GridGeom geom;
-    size_t elem;           // bytes per element
-    int cur = 0;           // buffer holding the current field
-    bool ghosts_dirty = true;          // ghost layer of the current buffer needs a refill
-    double ghost_lambda = 0.0, ghost_dx = 0.0;   // model the ghosts were filled with
-    TmaCache tma;                      // tensor maps of the two buffers
-    long long steps = 0;
-    double time = 0.0;
-    // model of the last step (stats: energy, estimator)
-    double M = 1.0, Gamma = 1.0, lambda = 0.0, dx = 1.0, dF = 0.0;
-    int stencil = 26, scheme = SPFM_TI_GLOBAL;
-    std::string err;
-};
-
 namespace spfm_host {
+
+void set_thread_error(const char *msg) { t_err = msg; }
 
 int fail(spfm_grid *g, int code, const char *fmt, ...)
 {
@@ -58,18 +44,6 @@ size_t elem_size(int dtype)
 {
     return dtype == SPFM_F64 ? 8 : (dtype == SPFM_F32 ? 4 : 2);
 }
-
-// Model coefficients in FP64 (a1).  gamma defaults, nu_j = 3/m_j, c_j, A_k
-// grouped by value, stability and phase checks.
-struct Model {
-    double gamma[3], w[kMaxTerms], c_shell[3], ck[kMaxTerms];
-    double a[kMaxTerms];
-    int nterms;
-    double beta[kMaxTerms], A[kMaxTerms];
-    double kmu, kappa, D, Cg;
-    double aface[6];
-    double bound;   // upper bound of the spectral radius of the Euler Jacobian
-};
 
 int n_dirs(int stencil) { return stencil == 6 ? 3 : (stencil == 18 ? 9 : 13); }
 
@@ -179,38 +153,73 @@ int build_model(spfm_grid *g, double M, double Gamma, double lambda, double dx, 
     return SPFM_OK;
 }
 
-template <class T>
-void fill_coef(const spfm_grid *g, const Model &m, double dt, int stencil, StepCoef<T> &c)
-{
-    memset(&c, 0, sizeof c);
-    c.g = g->geom;
-    for (int f = 0; f < 6; ++f) c.aface[f] = (T)m.aface[f];
-    c.c1 = (T)m.c_shell[0];
-    c.c2 = (T)m.c_shell[1];
-    c.c3 = (T)m.c_shell[2];
-    c.dt = (T)dt;
-    c.kmu = (T)m.kmu;
-    c.kappa = (T)m.kappa;
-    c.nterms = m.nterms;
-    for (int t = 0; t < kMaxTerms; ++t) {
-        c.beta[t] = t < m.nterms ? (T)m.beta[t] : T(0);
-        c.A[t] = t < m.nterms ? (T)m.A[t] : T(0);
-        c.ck[t] = (T)m.ck[t];
-        c.nbetadt[t] = t < m.nterms ? (T)(-m.beta[t] * dt) : T(0);
-    }
-    // S1 = F'_z + t, S2 = E'_z + F'_{z-1} + F'_{z+1} + 4t, S3 = E'_{z-1} + E'_{z+1} + 4t
-    double ct = m.c_shell[0];
-    if (stencil >= 18) ct += 4.0 * m.c_shell[1];
-    if (stencil == 26) ct += 4.0 * m.c_shell[2];
-    c.c1dt = (T)(m.c_shell[0] * dt);
-    c.c2dt = (T)(m.c_shell[1] * dt);
-    c.c3dt = (T)(m.c_shell[2] * dt);
-    c.ctdt = (T)(ct * dt);
-    c.nkmudt = (T)(-m.kmu * dt);
-    c.nkapdt = (T)(-m.kappa * dt);
-}
 
 cudaStream_t stream_of(const spfm_grid *g) { return (cudaStream_t)g->d.stream; }
+
+// Refill the ghost layer of the current buffer for the given lambda and dx
+// (contact faces depend on both), and clear the device error word.
+int refresh_ghosts(spfm_grid *g, double lambda, double dx)
+{
+    double af[6];
+    for (int f = 0; f < 6; ++f) {
+        const double sgn = (f % 2 == 0) ? -1.0 : 1.0;
+        af[f] = tanh(2.0 * sgn * dx * g->d.n[f / 2] / lambda);
+    }
+    cudaError_t e = launch_fill_ghosts(g->geom, g->d.dtype, af, g->d.field[g->cur], stream_of(g), 1);
+    if (e != cudaSuccess) return cuda_fail(g, e, "ghost fill");
+    g->ghosts_dirty = false;
+    g->ghost_lambda = lambda;
+    g->ghost_dx = dx;
+    return SPFM_OK;
+}
+
+int *err_word(const spfm_grid *g)
+{
+    return (int *)((char *)g->d.scratch + scratch_err_offset());
+}
+
+
+// Arguments of the stats pass over grid g (model of its last step or init).
+void fill_stats_args(const spfm_grid *g, int flags, StatsArgs &a)
+{
+    memset(&a, 0, sizeof a);
+    a.g = g->geom;
+    a.dtype = g->d.dtype;
+    for (int i = 0; i < 3; ++i) { a.n[i] = g->d.n[i]; a.ctr[i] = g->d.center[i]; }
+    a.lambda = g->lambda;
+    a.dx = g->dx;
+    a.energy = (flags & SPFM_STATS_ENERGY) && g->scheme != SPFM_TI_LOCAL ? 1 : 0;
+    a.scheme = g->scheme;
+    a.stencil = g->stencil;
+    a.Gamma = g->Gamma;
+    a.C_gamma = g->d.C_gamma > 0.0 ? g->d.C_gamma : 2.0 / 3.0;
+    double gam[3];
+    default_gamma(g->stencil, g->d.gamma, gam);
+    const double nu[3] = {1.0, 0.5, 0.75};
+    const int nd = n_dirs(g->stencil);
+    for (int k = 0; k < kMaxTerms; ++k) {
+        const Dir d = grid_dir(k);
+        a.w[k] = k < nd ? gam[d.shell - 1] * nu[d.shell - 1] : 0.0;
+        a.a[k] = tanh(2.0 * g->dx * (d.x * g->d.n[0] + d.y * g->d.n[1] + d.z * g->d.n[2]) / g->lambda);
+    }
+}
+
+// The public stats record from the kNStat reduced doubles of grid g.
+void stats_from_reduction(const spfm_grid *g, const double *h, int energy, spfm_stats *out)
+{
+    out->volume = h[0] * g->dx * g->dx * g->dx;
+    out->S_w = h[1];
+    out->S_c = h[2];
+    out->S_r = h[3];
+    out->phi_min = h[4];
+    out->phi_max = h[5];
+    out->nonfinite = h[6];
+    out->position = h[1] > 0.0 ? h[2] / h[1] : NAN;
+    out->radius = h[1] > 0.0 ? h[3] / h[1] : NAN;
+    out->energy = energy ? h[7] * g->dx * g->dx * g->dx : NAN;
+    out->steps = (double)g->steps;
+    out->time = g->time;
+}
 
 }  // namespace spfm_host
 
@@ -299,28 +308,6 @@ spfm_status spfm_set_stream(spfm_grid *g, void *stream)
 }
 
 int spfm_current(const spfm_grid *g) { return g ? g->cur : -1; }
-
-// Refill the ghost layer of the current buffer for the given lambda and dx
-// (contact faces depend on both), and clear the device error word.
-static spfm_status refresh_ghosts(spfm_grid *g, double lambda, double dx)
-{
-    double af[6];
-    for (int f = 0; f < 6; ++f) {
-        const double sgn = (f % 2 == 0) ? -1.0 : 1.0;
-        af[f] = tanh(2.0 * sgn * dx * g->d.n[f / 2] / lambda);
-    }
-    cudaError_t e = launch_fill_ghosts(g->geom, g->d.dtype, af, g->d.field[g->cur], stream_of(g), 1);
-    if (e != cudaSuccess) return cuda_fail(g, e, "ghost fill");
-    g->ghosts_dirty = false;
-    g->ghost_lambda = lambda;
-    g->ghost_dx = dx;
-    return SPFM_OK;
-}
-
-static int *err_word(const spfm_grid *g)
-{
-    return (int *)((char *)g->d.scratch + scratch_err_offset());
-}
 
 static spfm_status init_common(spfm_grid *g, InitArgs &a, double lambda, double dx)
 {
@@ -426,26 +413,7 @@ spfm_status spfm_interface_stats(spfm_grid *g, int flags, spfm_stats *out)
     if (!g || !out) return fail(g, SPFM_EINVAL, "spfm_interface_stats: NULL argument");
     if (!(g->lambda > 0.0)) return fail(g, SPFM_EINVAL, "spfm_interface_stats: no model yet (init or step first)");
     StatsArgs a;
-    memset(&a, 0, sizeof a);
-    a.g = g->geom;
-    a.dtype = g->d.dtype;
-    for (int i = 0; i < 3; ++i) { a.n[i] = g->d.n[i]; a.ctr[i] = g->d.center[i]; }
-    a.lambda = g->lambda;
-    a.dx = g->dx;
-    a.energy = (flags & SPFM_STATS_ENERGY) && g->scheme != SPFM_TI_LOCAL ? 1 : 0;
-    a.scheme = g->scheme;
-    a.stencil = g->stencil;
-    a.Gamma = g->Gamma;
-    a.C_gamma = g->d.C_gamma > 0.0 ? g->d.C_gamma : 2.0 / 3.0;
-    double gam[3];
-    default_gamma(g->stencil, g->d.gamma, gam);
-    const double nu[3] = {1.0, 0.5, 0.75};
-    const int nd = n_dirs(g->stencil);
-    for (int k = 0; k < kMaxTerms; ++k) {
-        const Dir d = grid_dir(k);
-        a.w[k] = k < nd ? gam[d.shell - 1] * nu[d.shell - 1] : 0.0;
-        a.a[k] = tanh(2.0 * g->dx * (d.x * g->d.n[0] + d.y * g->d.n[1] + d.z * g->d.n[2]) / g->lambda);
-    }
+    fill_stats_args(g, flags, a);
     if (a.energy && (g->ghosts_dirty || g->ghost_lambda != g->lambda || g->ghost_dx != g->dx)) {
         spfm_status st = refresh_ghosts(g, g->lambda, g->dx);
         if (st != SPFM_OK) return st;
@@ -461,18 +429,7 @@ spfm_status spfm_interface_stats(spfm_grid *g, int flags, spfm_stats *out)
     if (e != cudaSuccess) return cuda_fail(g, e, "spfm_interface_stats");
     int errw;
     memcpy(&errw, &h[kNStat], sizeof errw);
-    out->volume = h[0] * g->dx * g->dx * g->dx;
-    out->S_w = h[1];
-    out->S_c = h[2];
-    out->S_r = h[3];
-    out->phi_min = h[4];
-    out->phi_max = h[5];
-    out->nonfinite = h[6];
-    out->position = h[1] > 0.0 ? h[2] / h[1] : NAN;
-    out->radius = h[1] > 0.0 ? h[3] / h[1] : NAN;
-    out->energy = a.energy ? h[7] * g->dx * g->dx * g->dx : NAN;
-    out->steps = (double)g->steps;
-    out->time = g->time;
+    stats_from_reduction(g, h, a.energy, out);
     if (errw != 0)
         return fail(g, SPFM_ETIMEOUT, "a bounded wait in the step kernel gave up (code %d)", errw);
     if (h[6] > 0.0) return fail(g, SPFM_ENONFINITE, "field holds %.0f non-finite cells", h[6]);

@@ -1,18 +1,332 @@
-// batch.cu -- many grids per launch (placeholder until the work-list kernel lands).
-#include "spfm_internal.h"
+// batch.cu -- the batch calls of the C ABI.
+//
+// Many grids of one storage type advance together: every step is one launch of
+// the persistent step kernel over a packed tile work-list of all grids (each
+// item: grid, tile column/row, z range of at most kBatchZChunk planes) plus one
+// launch of the ghost-face kernel over all grids.  The per-grid records (step
+// coefficients, buffers, TMA maps) live in the caller's scratch and are read
+// by the kernels at run time, so a captured CUDA graph of kGraphSteps steps is
+// replayed unchanged across calls; parameters can change between calls.  Each
+// grid's arithmetic is exactly the single-grid step's.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "host_internal.h"
+
+using namespace spfm;
+using namespace spfm_host;
+
+namespace {
+
+constexpr int kBatchZChunk = 32;
+constexpr int kGraphSteps = 16;   // steps per captured graph (even: parity repeats)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Layout {
+    size_t grids, items, ghosts, stats_jobs, partials, finals, err, total;
+};
+
+size_t grid_record_bytes(int dtype)
+{
+    return dtype == SPFM_F64 ? batch_grid_bytes_f64()
+                             : (dtype == SPFM_F32 ? batch_grid_bytes_f32() : batch_grid_bytes_bf16());
+}
+
+int items_of(int dtype, const GridGeom &g, int gi, BatchItem *out)
+{
+    return dtype == SPFM_F64   ? batch_items_f64(g, gi, kBatchZChunk, out)
+           : dtype == SPFM_F32 ? batch_items_f32(g, gi, kBatchZChunk, out)
+                               : batch_items_bf16(g, gi, kBatchZChunk, out);
+}
+
+Layout layout_for(int dtype, int n, int nitems)
+{
+    Layout L;
+    size_t off = 0;
+    L.grids = off;
+    off = align_up(off + grid_record_bytes(dtype) * n, 256);
+    L.items = off;
+    off = align_up(off + sizeof(BatchItem) * nitems, 256);
+    L.ghosts = off;
+    off = align_up(off + sizeof(GhostJob) * n, 256);
+    L.stats_jobs = off;
+    off = align_up(off + sizeof(StatsJob) * n, 256);
+    L.partials = off;
+    off = align_up(off + sizeof(double) * kNStat * kBatchStatsBlocks * n, 256);
+    L.finals = off;
+    off = align_up(off + sizeof(double) * (kNStat * n + 1), 256);
+    L.err = off;
+    off = align_up(off + 16, 256);
+    L.total = off;
+    return L;
+}
+
+int check_grids(spfm_grid *const *grids, int n, int *dtype, int *nitems)
+{
+    if (!grids || n < 1) return fail(nullptr, SPFM_EINVAL, "spfm_batch: need at least one grid");
+    int items = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!grids[i]) return fail(nullptr, SPFM_EINVAL, "spfm_batch: grid %d is NULL", i);
+        if (grids[i]->d.dtype != grids[0]->d.dtype)
+            return fail(nullptr, SPFM_EINVAL, "spfm_batch: grid %d has another dtype", i);
+        for (int j = 0; j < i; ++j)
+            if (grids[j] == grids[i]) return fail(nullptr, SPFM_EINVAL, "spfm_batch: grid %d repeated", i);
+        items += items_of(grids[i]->d.dtype, grids[i]->geom, i, nullptr);
+    }
+    *dtype = grids[0]->d.dtype;
+    *nitems = items;
+    return SPFM_OK;
+}
+
+}  // namespace
+
+struct spfm_batch {
+    std::vector<spfm_grid *> grids;
+    int n = 0, dtype = 0, nitems = 0;
+    char *scratch = nullptr;
+    cudaStream_t stream = nullptr;
+    Layout L;
+    std::vector<BatchItem> h_items;
+    std::vector<char> h_grids;
+    std::vector<GhostJob> h_ghosts;
+    std::vector<StatsJob> h_stats;
+    std::vector<double> h_finals;
+    cudaGraphExec_t exec = nullptr;
+    int graph_stencil = -1, graph_kind = -1;
+    std::string err;
+    ~spfm_batch()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
+
+static int bfail(spfm_batch *b, int code, const char *msg)
+{
+    if (b) b->err = msg;
+    return fail(nullptr, code, "%s", msg);
+}
+
+// one step of every grid: persistent step kernel, then the ghost faces of the
+// buffers it wrote
+static cudaError_t launch_one(spfm_batch *b, int parity, int stencil, int kind)
+{
+    const void *grids = b->scratch + b->L.grids;
+    const BatchItem *items = (const BatchItem *)(b->scratch + b->L.items);
+    int *err = (int *)(b->scratch + b->L.err);
+    cudaError_t e;
+    if (b->dtype == SPFM_F64) e = launch_batch_f64(grids, items, b->nitems, parity, err, stencil, kind, b->stream);
+    else if (b->dtype == SPFM_F32) e = launch_batch_f32(grids, items, b->nitems, parity, err, stencil, kind, b->stream);
+    else e = launch_batch_bf16(grids, items, b->nitems, parity, err, stencil, kind, b->stream);
+    if (e != cudaSuccess) return e;
+    return launch_fill_ghosts_batch((const GhostJob *)(b->scratch + b->L.ghosts), b->n, b->dtype,
+                                    parity ^ 1, b->stream);
+}
+
+static cudaError_t capture_graph(spfm_batch *b, int stencil, int kind)
+{
+    if (b->exec && b->graph_stencil == stencil && b->graph_kind == kind) return cudaSuccess;
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t le = cudaSuccess;
+    for (int s = 0; s < kGraphSteps && le == cudaSuccess; ++s) le = launch_one(b, s & 1, stencil, kind);
+    e = cudaStreamEndCapture(b->stream, &graph);
+    if (le != cudaSuccess) e = le;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e == cudaSuccess) {
+        b->graph_stencil = stencil;
+        b->graph_kind = kind;
+    } else {
+        b->exec = nullptr;
+    }
+    return e;
+}
 
 extern "C" {
-spfm_status spfm_batch_scratch_bytes(spfm_grid *const *, int, size_t *bytes)
+
+spfm_status spfm_batch_scratch_bytes(spfm_grid *const *grids, int n, size_t *bytes)
 {
-    if (bytes) *bytes = 0;
-    return SPFM_EINVAL;
+    int dtype = 0, nitems = 0;
+    spfm_status st = check_grids(grids, n, &dtype, &nitems);
+    if (st != SPFM_OK) return st;
+    if (bytes) *bytes = layout_for(dtype, n, nitems).total;
+    return SPFM_OK;
 }
-spfm_status spfm_batch_create(spfm_grid *const *, int, void *, size_t, void *, spfm_batch **out)
+
+spfm_status spfm_batch_create(spfm_grid *const *grids, int n, void *scratch, size_t scratch_bytes,
+                              void *stream, spfm_batch **out)
 {
-    if (out) *out = nullptr;
-    return SPFM_EINVAL;
+    if (!out) return fail(nullptr, SPFM_EINVAL, "spfm_batch_create: out is NULL");
+    *out = nullptr;
+    int dtype = 0, nitems = 0;
+    spfm_status st = check_grids(grids, n, &dtype, &nitems);
+    if (st != SPFM_OK) return st;
+    const Layout L = layout_for(dtype, n, nitems);
+    if (!scratch || ((uintptr_t)scratch & 255) || scratch_bytes < L.total)
+        return fail(nullptr, SPFM_ENOMEM, "spfm_batch_create: scratch NULL, not 256-byte aligned or below %zu bytes",
+                    L.total);
+    spfm_batch *b = new spfm_batch();
+    b->grids.assign(grids, grids + n);
+    b->n = n;
+    b->dtype = dtype;
+    b->nitems = nitems;
+    b->scratch = (char *)scratch;
+    b->stream = (cudaStream_t)stream;
+    b->L = L;
+    b->h_items.resize(nitems);
+    int k = 0;
+    for (int i = 0; i < n; ++i) k += items_of(dtype, grids[i]->geom, i, b->h_items.data() + k);
+    b->h_grids.assign(grid_record_bytes(dtype) * n, 0);
+    b->h_ghosts.resize(n);
+    b->h_stats.resize(n);
+    b->h_finals.resize((size_t)kNStat * n + 1);
+    cudaError_t e = cudaMemcpyAsync(b->scratch + L.items, b->h_items.data(), sizeof(BatchItem) * nitems,
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->scratch + L.err, 0, 16, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        delete b;
+        return fail(nullptr, SPFM_ECUDA, "spfm_batch_create: %s", cudaGetErrorString(e));
+    }
+    *out = b;
+    return SPFM_OK;
 }
-spfm_status spfm_batch_step(spfm_batch *, int, const spfm_step_args *) { return SPFM_EINVAL; }
-spfm_status spfm_batch_stats(spfm_batch *, int, spfm_stats *) { return SPFM_EINVAL; }
-spfm_status spfm_batch_destroy(spfm_batch *) { return SPFM_OK; }
+
+spfm_status spfm_batch_step(spfm_batch *b, int n_steps, const spfm_step_args *args)
+{
+    if (!b || !args) return fail(nullptr, SPFM_EINVAL, "spfm_batch_step: NULL argument");
+    if (n_steps < 0) return bfail(b, SPFM_EINVAL, "spfm_batch_step: n_steps < 0");
+    const int stencil = args[0].stencil, scheme = args[0].scheme;
+    if (scheme == SPFM_TI_LOCAL)
+        return bfail(b, SPFM_EINVAL, "spfm_batch_step: SPFM_TI_LOCAL is not available for batches");
+    const size_t rec = grid_record_bytes(b->dtype);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < b->n; ++i) {
+        spfm_grid *g = b->grids[i];
+        const spfm_step_args &a = args[i];
+        if (a.stencil != stencil || a.scheme != scheme)
+            return bfail(b, SPFM_EINVAL, "spfm_batch_step: all grids of a batch share stencil and scheme");
+        Model m;
+        spfm_status st = build_model(g, a.M, a.Gamma, a.lambda, a.dx, a.dt, a.dF, a.stencil, a.scheme, m);
+        if (st != SPFM_OK) {
+            char msg[600];
+            snprintf(msg, sizeof msg, "grid %d: %s", i, g->err.c_str());
+            return bfail(b, st, msg);
+        }
+        if (n_steps > 0 && (g->ghosts_dirty || g->ghost_lambda != a.lambda || g->ghost_dx != a.dx)) {
+            e = launch_fill_ghosts(g->geom, g->d.dtype, m.aface, g->d.field[g->cur], b->stream, 1);
+            if (e != cudaSuccess) return bfail(b, SPFM_ECUDA, cudaGetErrorString(e));
+            g->ghosts_dirty = false;
+            g->ghost_lambda = a.lambda;
+            g->ghost_dx = a.dx;
+        }
+        void *slot = b->h_grids.data() + rec * i;
+        if (b->dtype == SPFM_F64) {
+            StepCoef<double> c;
+            fill_coef<double>(g, m, a.dt, a.stencil, c);
+            batch_fill_grid_f64(slot, c, g->d.field, g->cur, &g->tma);
+        } else {
+            StepCoef<float> c;
+            fill_coef<float>(g, m, a.dt, a.stencil, c);
+            if (b->dtype == SPFM_F32) batch_fill_grid_f32(slot, c, g->d.field, g->cur, &g->tma);
+            else batch_fill_grid_bf16(slot, c, g->d.field, g->cur, &g->tma);
+        }
+        GhostJob &gj = b->h_ghosts[i];
+        gj.g = g->geom;
+        for (int f = 0; f < 6; ++f) gj.aface[f] = m.aface[f];
+        gj.field[0] = g->d.field[0];
+        gj.field[1] = g->d.field[1];
+        gj.cur = g->cur;
+    }
+    if (n_steps == 0) return SPFM_OK;
+    const int kind = scheme == SPFM_FD ? 0 : 5;
+    e = cudaMemcpyAsync(b->scratch + b->L.grids, b->h_grids.data(), rec * b->n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->scratch + b->L.ghosts, b->h_ghosts.data(), sizeof(GhostJob) * b->n,
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) return bfail(b, SPFM_ECUDA, cudaGetErrorString(e));
+    int s = 0;
+    // graphs need a capturable stream (not the legacy default stream)
+    if (n_steps >= kGraphSteps && b->stream != nullptr) {
+        e = capture_graph(b, stencil, kind);
+        if (e != cudaSuccess) return bfail(b, SPFM_ECUDA, cudaGetErrorString(e));
+        for (; s + kGraphSteps <= n_steps; s += kGraphSteps) {
+            e = cudaGraphLaunch(b->exec, b->stream);
+            if (e != cudaSuccess) return bfail(b, SPFM_ECUDA, cudaGetErrorString(e));
+        }
+    }
+    for (; s < n_steps; ++s) {
+        e = launch_one(b, s & 1, stencil, kind);
+        if (e != cudaSuccess) return bfail(b, SPFM_ECUDA, cudaGetErrorString(e));
+    }
+    for (int i = 0; i < b->n; ++i) {
+        spfm_grid *g = b->grids[i];
+        const spfm_step_args &a = args[i];
+        g->cur ^= (n_steps & 1);
+        g->steps += n_steps;
+        g->time += n_steps * a.dt;
+        g->M = a.M;
+        g->Gamma = a.Gamma;
+        g->lambda = a.lambda;
+        g->dx = a.dx;
+        g->dF = a.dF;
+        g->stencil = a.stencil;
+        g->scheme = a.scheme;
+    }
+    return SPFM_OK;
 }
+
+spfm_status spfm_batch_stats(spfm_batch *b, int flags, spfm_stats *out)
+{
+    if (!b || !out) return fail(nullptr, SPFM_EINVAL, "spfm_batch_stats: NULL argument");
+    for (int i = 0; i < b->n; ++i) {
+        spfm_grid *g = b->grids[i];
+        if (!(g->lambda > 0.0)) return bfail(b, SPFM_EINVAL, "spfm_batch_stats: a grid has no model yet");
+        StatsJob &j = b->h_stats[i];
+        fill_stats_args(g, flags, j.a);
+        if (j.a.energy && (g->ghosts_dirty || g->ghost_lambda != g->lambda || g->ghost_dx != g->dx))
+            return bfail(b, SPFM_EINVAL, "spfm_batch_stats: energy needs valid ghosts (step the batch first)");
+        j.field[0] = g->d.field[0];
+        j.field[1] = g->d.field[1];
+        j.cur = g->cur;
+    }
+    double *finals = (double *)(b->scratch + b->L.finals);
+    cudaError_t e = cudaMemcpyAsync(b->scratch + b->L.stats_jobs, b->h_stats.data(), sizeof(StatsJob) * b->n,
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = launch_stats_batch((const StatsJob *)(b->scratch + b->L.stats_jobs), b->n, b->dtype,
+                               (double *)(b->scratch + b->L.partials), finals, b->stream);
+    // the error word sits right after the finals region: copy both
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->h_finals.data(), finals, sizeof(double) * kNStat * b->n, cudaMemcpyDeviceToHost,
+                            b->stream);
+    int errw = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&errw, b->scratch + b->L.err, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, SPFM_ECUDA, cudaGetErrorString(e));
+    double nonfinite = 0.0;
+    for (int i = 0; i < b->n; ++i) {
+        stats_from_reduction(b->grids[i], b->h_finals.data() + (size_t)kNStat * i, b->h_stats[i].a.energy, &out[i]);
+        nonfinite += out[i].nonfinite;
+    }
+    if (errw != 0) return bfail(b, SPFM_ETIMEOUT, "a bounded wait in the batch step kernel gave up");
+    if (nonfinite > 0.0) return bfail(b, SPFM_ENONFINITE, "a grid of the batch holds non-finite cells");
+    return SPFM_OK;
+}
+
+spfm_status spfm_batch_destroy(spfm_batch *b)
+{
+    delete b;
+    return SPFM_OK;
+}
+
+}  // extern "C"

@@ -34,13 +34,12 @@ struct FaceArgs {
 };
 
 template <class S>
-__global__ void __launch_bounds__(256) ghost_kernel(const FaceArgs a, S *f)
+__device__ __forceinline__ void ghost_faces(const FaceArgs &a, S *f, long long t0, long long stride)
 {
     using T = typename Cmp<S>::T;
     const GridGeom &g = a.g;
     const long long total = a.nzf + a.nyf + a.nxf;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
+    for (long long t = t0; t < total; t += stride) {
         int i, j, k;
         if (t < a.nzf) {
             const int u = (int)t, side = u >= a.zper, r = u - side * a.zper;
@@ -70,8 +69,14 @@ __global__ void __launch_bounds__(256) ghost_kernel(const FaceArgs a, S *f)
     }
 }
 
-cudaError_t launch_fill_ghosts(const GridGeom &g, int dtype, const double aface[6], void *field,
-                               cudaStream_t st, int x_faces)
+template <class S>
+__global__ void __launch_bounds__(256) ghost_kernel(const FaceArgs a, S *f)
+{
+    ghost_faces<S>(a, f, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                   (long long)gridDim.x * blockDim.x);
+}
+
+__host__ __device__ inline FaceArgs face_args(const GridGeom &g, const double *aface, int x_faces)
 {
     FaceArgs a;
     a.g = g;
@@ -82,6 +87,33 @@ cudaError_t launch_fill_ghosts(const GridGeom &g, int dtype, const double aface[
     a.nzf = 2LL * a.zper;
     a.nyf = 2LL * a.yper;
     a.nxf = x_faces ? 2LL * a.xper : 0;
+    return a;
+}
+
+// blockIdx.y selects the grid of the batch
+template <class S>
+__global__ void __launch_bounds__(256) ghost_batch_kernel(const GhostJob *jobs, int parity)
+{
+    const GhostJob &j = jobs[blockIdx.y];
+    const FaceArgs a = face_args(j.g, j.aface, 1);
+    ghost_faces<S>(a, (S *)j.field[j.cur ^ parity], blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                   (long long)gridDim.x * blockDim.x);
+}
+
+cudaError_t launch_fill_ghosts_batch(const GhostJob *jobs, int n, int dtype, int parity, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const dim3 grid(16, n);
+    if (dtype == SPFM_F64) ghost_batch_kernel<double><<<grid, 256, 0, st>>>(jobs, parity);
+    else if (dtype == SPFM_F32) ghost_batch_kernel<float><<<grid, 256, 0, st>>>(jobs, parity);
+    else ghost_batch_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(jobs, parity);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_ghosts(const GridGeom &g, int dtype, const double aface[6], void *field,
+                               cudaStream_t st, int x_faces)
+{
+    const FaceArgs a = face_args(g, aface, x_faces);
     const long long total = a.nzf + a.nyf + a.nxf;
     long long blocks = (total + 255) / 256;
     if (blocks > 2 * 152 * 8) blocks = 2 * 152 * 8;

@@ -177,4 +177,51 @@ inline size_t scratch_final_offset() { return sizeof(double) * (size_t)kNStat * 
 inline size_t scratch_err_offset() { return sizeof(double) * (size_t)kNStat * (kStatsBlocks + 1); }
 size_t grid_scratch_bytes();
 
+// ---------------------------------------------------------------- batches
+
+// One tile of a batch's packed work-list: grid, tile column/row, z range.
+struct BatchItem {
+    int grid, bx, by, zc0, zc1;
+};
+
+// Per-dtype pieces of the persistent batch kernel (step_f32.cu / ...):
+// bytes of one device-side grid record, the work-list items of one grid, the
+// record of one grid, and the launch of one step over the whole work-list
+// (kind: 0 CF, else TI with up to 13 groups).
+size_t batch_grid_bytes_f32();
+size_t batch_grid_bytes_f64();
+size_t batch_grid_bytes_bf16();
+int batch_items_f32(const GridGeom &g, int grid_index, int zchunk, BatchItem *out);
+int batch_items_f64(const GridGeom &g, int grid_index, int zchunk, BatchItem *out);
+int batch_items_bf16(const GridGeom &g, int grid_index, int zchunk, BatchItem *out);
+void batch_fill_grid_f32(void *slot, const StepCoef<float> &c, void *const field[2], int cur, TmaCache *tma);
+void batch_fill_grid_f64(void *slot, const StepCoef<double> &c, void *const field[2], int cur, TmaCache *tma);
+void batch_fill_grid_bf16(void *slot, const StepCoef<float> &c, void *const field[2], int cur, TmaCache *tma);
+cudaError_t launch_batch_f32(const void *grids, const BatchItem *work, int nwork, int parity, int *err,
+                             int stencil, int kind, cudaStream_t st);
+cudaError_t launch_batch_f64(const void *grids, const BatchItem *work, int nwork, int parity, int *err,
+                             int stencil, int kind, cudaStream_t st);
+cudaError_t launch_batch_bf16(const void *grids, const BatchItem *work, int nwork, int parity, int *err,
+                              int stencil, int kind, cudaStream_t st);
+
+// Ghost refresh of every grid of a batch: job i fills buffer cur ^ parity of grid i.
+struct GhostJob {
+    GridGeom g;
+    double aface[6];
+    void *field[2];
+    int cur;
+};
+cudaError_t launch_fill_ghosts_batch(const GhostJob *jobs, int n, int dtype, int parity, cudaStream_t st);
+
+// Diagnostics of every grid of a batch: job i reads buffer cur of grid i; the
+// final reduction of grid i lands in finals[i * kNStat ..].
+struct StatsJob {
+    StatsArgs a;
+    const void *field[2];
+    int cur;
+};
+constexpr int kBatchStatsBlocks = 32;   // partial blocks per grid
+cudaError_t launch_stats_batch(const StatsJob *jobs, int n, int dtype, double *partials, double *finals,
+                               cudaStream_t st);
+
 }  // namespace spfm

@@ -117,7 +117,8 @@ __device__ __forceinline__ void block_reduce_store(double *v, double *out)
 // Per-thread partials: [0] sum phi, [1] S_w, [2] S_c, [3] S_r, [4] min, [5] max,
 // [6] non-finite count, [7] energy density sum, [8..11] unused.
 template <class S>
-__global__ void __launch_bounds__(256) stats_kernel(const StatsArgs a, const S *f, double *partials)
+__device__ __forceinline__ void stats_pass(const StatsArgs &a, const S *f, double *partial_out,
+                                           long long row0, long long row_stride)
 {
     double v[kNStat];
 #pragma unroll
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(256) stats_kernel(const StatsArgs a, const S *
     const double e_pref = a.Gamma / (a.C_gamma * a.lambda);
     const int nd = a.stencil == 6 ? 3 : (a.stencil == 18 ? 9 : 13);
     const long long rows = (long long)a.g.ny * a.g.nz;
-    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    for (long long row = row0; row < rows; row += row_stride) {
         const int j = (int)(row % a.g.ny);
         const int k = (int)(row / a.g.ny);
         const long long rbase = cell_index(a.g, 0, j, k);
@@ -161,11 +162,30 @@ __global__ void __launch_bounds__(256) stats_kernel(const StatsArgs a, const S *
             }
         }
     }
-    block_reduce_store(v, partials + (long long)blockIdx.x * kNStat);
+    block_reduce_store(v, partial_out);
 }
 
+template <class S>
+__global__ void __launch_bounds__(256) stats_kernel(const StatsArgs a, const S *f, double *partials)
+{
+    stats_pass<S>(a, f, partials + (long long)blockIdx.x * kNStat, blockIdx.x, gridDim.x);
+}
+
+// blockIdx.y selects the grid of the batch
+template <class S>
+__global__ void __launch_bounds__(256) stats_batch_kernel(const StatsJob *jobs, double *partials)
+{
+    const StatsJob &j = jobs[blockIdx.y];
+    stats_pass<S>(j.a, (const S *)j.field[j.cur],
+                  partials + ((long long)blockIdx.y * kBatchStatsBlocks + blockIdx.x) * kNStat,
+                  blockIdx.x, gridDim.x);
+}
+
+// blockIdx.x selects a grid: reduce its nblocks partials into out[blockIdx.x]
 __global__ void __launch_bounds__(256) stats_final_kernel(const double *partials, int nblocks, double *out)
 {
+    partials += (long long)blockIdx.x * nblocks * kNStat;
+    out += (long long)blockIdx.x * kNStat;
     double v[kNStat];
 #pragma unroll
     for (int i = 0; i < kNStat; ++i) v[i] = 0.0;
@@ -205,6 +225,20 @@ cudaError_t launch_stats(const StatsArgs &a, const void *field, double *partials
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     stats_final_kernel<<<1, 256, 0, st>>>(partials, kStatsBlocks, final_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stats_batch(const StatsJob *jobs, int n, int dtype, double *partials, double *finals,
+                               cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const dim3 grid(kBatchStatsBlocks, n);
+    if (dtype == SPFM_F64) stats_batch_kernel<double><<<grid, 256, 0, st>>>(jobs, partials);
+    else if (dtype == SPFM_F32) stats_batch_kernel<float><<<grid, 256, 0, st>>>(jobs, partials);
+    else stats_batch_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(jobs, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    stats_final_kernel<<<n, 256, 0, st>>>(partials, kBatchStatsBlocks, finals);
     return cudaGetLastError();
 }
 

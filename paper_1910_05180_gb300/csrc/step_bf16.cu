@@ -9,4 +9,36 @@ cudaError_t launch_step_bf16(const StepCoef<float> &c, const __nv_bfloat16 *src,
     const CUtensorMap *map = cached_map(tma, which, c.g, SPFM_BF16, src, Sh::SW, Sh::ROWS);
     return launch_step_t<__nv_bfloat16, float, 8, 16>(c, src, dst, err, cfg, map, st);
 }
+
+size_t batch_grid_bytes_bf16() { return sizeof(BatchGrid<float>); }
+
+int batch_items_bf16(const GridGeom &g, int grid_index, int zchunk, BatchItem *out)
+{
+    return batch_items_t<__nv_bfloat16, float, 8, 16>(g, grid_index, zchunk, out);
+}
+
+void batch_fill_grid_bf16(void *slot, const StepCoef<float> &c, void *const field[2], int cur,
+                          TmaCache *tma)
+{
+    using Sh = TileShape<__nv_bfloat16, float, 8, 16>;
+    BatchGrid<float> *b = (BatchGrid<float> *)slot;
+    b->C = c;
+    b->PC = make_pack_coef<float>(c);
+    b->field[0] = field[0];
+    b->field[1] = field[1];
+    b->cur = cur;
+    const CUtensorMap *m0 = cached_map(tma, 0, c.g, SPFM_BF16, field[0], Sh::SW, Sh::ROWS);
+    const CUtensorMap *m1 = cached_map(tma, 1, c.g, SPFM_BF16, field[1], Sh::SW, Sh::ROWS);
+    b->has_map = (m0 && m1) ? 1 : 0;
+    if (b->has_map) {
+        b->map[0] = *m0;
+        b->map[1] = *m1;
+    }
+}
+
+cudaError_t launch_batch_bf16(const void *grids, const BatchItem *work, int nwork, int parity,
+                              int *err, int stencil, int kind, cudaStream_t st)
+{
+    return launch_batch_t<__nv_bfloat16, float, 8, 16>(grids, work, nwork, parity, err, stencil, kind, st);
+}
 }  // namespace spfm

@@ -313,12 +313,16 @@ __device__ __forceinline__ void get_row(const S *r, typename Pk<T>::P *c, typena
 
 // KIND: 0 = CF potential; 1..4 = TI global with exactly KIND coupling groups;
 // 5 = TI global with up to 13 groups (count read at run time)
+// One tile (bx, by) of planes zc0..zc1-1.  The stage ring continues across the
+// tiles a CTA processes: plane i of this tile is ring slot base + i.  The
+// producer waits for its copies in flight before returning when drain is set.
+// Returns false when a bounded wait gave up (the error word is set).
 template <class S, class T, int STENCIL, int KIND, int TX, int TY>
-__device__ __forceinline__ void step_tile(const StepCoef<T> &C, const PackCoef<T> &PC,
+__device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T> &PC,
                                           const S *__restrict__ src, S *__restrict__ dst,
                                           int *__restrict__ err, const CUtensorMap *tmap, int bx,
                                           int by, int zc0, int zc1, S *__restrict__ stages,
-                                          uint64_t *full, uint64_t *empty)
+                                          uint64_t *full, uint64_t *empty, int base, bool drain)
 {
     using Sh = TileShape<S, T, TX, TY>;
     using K = Pk<T>;
@@ -334,12 +338,12 @@ __device__ __forceinline__ void step_tile(const StepCoef<T> &C, const PackCoef<T
 
     if (tid >= Sh::NCONS) {
         // ------------------------------------------------------- producer warp
-        if (tid != Sh::NCONS) return;
+        if (tid != Sh::NCONS) return true;
         int issued = 0;
         bool ok = true;
         for (int i = 0; i < nplanes; ++i) {
-            const int s = i % NS;
-            if (i >= NS && !mbar_wait_sleep(&empty[s], ((i / NS) - 1) & 1)) { ok = false; break; }
+            const int I = base + i, s = I % NS;
+            if (I >= NS && !mbar_wait_sleep(&empty[s], ((I / NS) - 1) & 1)) { ok = false; break; }
             if (tmap) {
                 mbar_expect_tx(&full[s], (uint32_t)Sh::BOX_BYTES);
                 // one box: padded x from the left halo chunk (x0), padded rows y0..,
@@ -360,9 +364,10 @@ __device__ __forceinline__ void step_tile(const StepCoef<T> &C, const PackCoef<T
         }
         if (!ok) atomicOr(err, 1);
         // never leave with copies in flight
-        for (int i = max(0, issued - NS); i < issued; ++i)
-            if (!mbar_wait_sleep(&full[i % NS], (i / NS) & 1)) { atomicOr(err, 2); break; }
-        return;
+        if (drain || !ok)
+            for (int I = max(0, base + issued - NS); I < base + issued; ++I)
+                if (!mbar_wait_sleep(&full[I % NS], (I / NS) & 1)) { atomicOr(err, 2); break; }
+        return ok;
     }
 
     // ------------------------------------------------------------- consumers
@@ -374,12 +379,14 @@ __device__ __forceinline__ void step_tile(const StepCoef<T> &C, const PackCoef<T
     const S *rbase = stages + (ty + 1) * SW + VX + tx * VX;   // first own row in a stage
     S *obase = dst + cell_index(g, gx, gy, 0);                // plane 0, first own row
 
+    bool ok = true;
     auto body = [&](int i, PlaneQ<T, NP> (&m)[RPT], PlaneQ<T, NP> (&z)[RPT],
                     PlaneQ<T, NP> (&p)[RPT]) -> bool {
-        const int s = i % NS;
+        const int I = base + i, s = I % NS;
         // warp-uniform: every lane waits (acquire), the warp goes on only if all saw it
-        if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (i / NS) & 1))) {
+        if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (I / NS) & 1))) {
             if (lane == 0) atomicOr(err, 4);
+            ok = false;
             return false;
         }
         {
@@ -464,6 +471,7 @@ __device__ __forceinline__ void step_tile(const StepCoef<T> &C, const PackCoef<T
         if (!body(i + 1, q2, q0, q1)) break;
         if (!body(i + 2, q0, q1, q2)) break;
     }
+    return ok;
 }
 
 // minimum resident CTAs per SM (two 288-thread CTAs leave 113 registers a thread)
@@ -489,7 +497,99 @@ __global__ void __launch_bounds__(TileShape<S, T, TX, TY>::NTHREADS, MinBlocks<S
     const int zc0 = blockIdx.z * zchunk;
     const int zc1 = min(zc0 + zchunk, C.g.nz);
     step_tile<S, T, STENCIL, KIND, TX, TY>(C, PC, src, dst, err, use_tmap ? &tmap : nullptr,
-                                           blockIdx.x, blockIdx.y, zc0, zc1, stages, full, empty);
+                                           blockIdx.x, blockIdx.y, zc0, zc1, stages, full, empty, 0,
+                                           true);
+}
+
+// ------------------------------------------------------------------- batches
+
+// One grid of a batch as the persistent kernel reads it from device memory.
+template <class T>
+struct BatchGrid {
+    CUtensorMap map[2];     // TMA maps of the two buffers (when has_map)
+    StepCoef<T> C;
+    PackCoef<T> PC;
+    void *field[2];
+    int cur;                // buffer holding the field at parity 0
+    int has_map;
+};
+
+// Persistent kernel over the packed work-list of all grids of a batch: CTA b
+// takes items b, b + gridDim.x, ...  Step `parity` reads buffer cur ^ parity.
+template <class S, class T, int STENCIL, int KIND, int TX, int TY>
+__global__ void __launch_bounds__(TileShape<S, T, TX, TY>::NTHREADS, MinBlocks<S>::value)
+    spfm_batch_kernel(const BatchGrid<T> *__restrict__ grids, const BatchItem *__restrict__ work,
+                      int nwork, int parity, int *__restrict__ err)
+{
+    using Sh = TileShape<S, T, TX, TY>;
+    __shared__ __align__(128) S stages[Sh::NS * Sh::STAGE];
+    __shared__ __align__(8) uint64_t full[Sh::NS], empty[Sh::NS];
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < Sh::NS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], Sh::NCONS / 32);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    int base = 0;
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+        const BatchItem it = work[w];
+        const BatchGrid<T> &bg = grids[it.grid];
+        const int cur = bg.cur ^ parity;
+        const CUtensorMap *map = bg.has_map ? &bg.map[cur] : nullptr;
+        if (map && threadIdx.x == Sh::NCONS)
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+        const bool last = w + (int)gridDim.x >= nwork;
+        if (!step_tile<S, T, STENCIL, KIND, TX, TY>(bg.C, bg.PC, (const S *)bg.field[cur],
+                                                    (S *)bg.field[cur ^ 1], err, map, it.bx, it.by,
+                                                    it.zc0, it.zc1, stages, full, empty, base, last))
+            return;
+        base += it.zc1 - it.zc0 + 2;
+    }
+}
+
+// Work-list entries of one grid for the tile shape of the (S, T) kernel.
+template <class S, class T, int TX, int TY>
+inline int batch_items_t(const GridGeom &g, int grid_index, int zchunk, BatchItem *out)
+{
+    using Sh = TileShape<S, T, TX, TY>;
+    const int gxn = (g.nx + Sh::W - 1) / Sh::W, gyn = (g.ny + TY - 1) / TY;
+    int n = 0;
+    for (int z = 0; z < g.nz; z += zchunk)
+        for (int by = 0; by < gyn; ++by)
+            for (int bx = 0; bx < gxn; ++bx) {
+                if (out) out[n] = BatchItem{grid_index, bx, by, z, min(z + zchunk, g.nz)};
+                ++n;
+            }
+    return n;
+}
+
+template <class S, class T, int TX, int TY>
+cudaError_t launch_batch_t(const void *grids, const BatchItem *work, int nwork, int parity, int *err,
+                           int stencil, int kind, cudaStream_t st)
+{
+    using Sh = TileShape<S, T, TX, TY>;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int ctas = sms * MinBlocks<S>::value;
+    if (ctas > nwork) ctas = nwork;
+    if (ctas < 1) return cudaSuccess;
+    const BatchGrid<T> *bg = (const BatchGrid<T> *)grids;
+#define SPFM_BLAUNCH(ST, KD) \
+    spfm_batch_kernel<S, T, ST, KD, TX, TY><<<ctas, Sh::NTHREADS, 0, st>>>(bg, work, nwork, parity, err)
+#define SPFM_BBY_KIND(ST)                      \
+    do {                                       \
+        if (kind == 0) SPFM_BLAUNCH(ST, 0);    \
+        else SPFM_BLAUNCH(ST, 5);              \
+    } while (0)
+    if (stencil == 6) SPFM_BBY_KIND(6);
+    else if (stencil == 18) SPFM_BBY_KIND(18);
+    else SPFM_BBY_KIND(26);
+#undef SPFM_BBY_KIND
+#undef SPFM_BLAUNCH
+    return cudaGetLastError();
 }
 
 // z-chunk length so that the launch has enough CTAs for 152 SMs

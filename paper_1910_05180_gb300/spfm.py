@@ -268,3 +268,75 @@ class Grid:
         src = src.contiguous()
         assert tuple(src.shape) == self.shape and src.dtype == TORCH_DTYPE[self.dtype]
         spfm_set_field(self.handle, src.data_ptr(), 0 if src.is_cuda else 1)
+
+
+# ------------------------------------------------------------------ batches
+
+def spfm_batch_scratch_bytes(handles) -> int:
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    n = ctypes.c_size_t()
+    _check(load().spfm_batch_scratch_bytes(arr, len(handles), ctypes.byref(n)))
+    return n.value
+
+
+def spfm_batch_create(handles, scratch_ptr, scratch_bytes, stream):
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    b = ctypes.c_void_p()
+    _check(load().spfm_batch_create(arr, len(handles), scratch_ptr, scratch_bytes, stream, ctypes.byref(b)))
+    return b
+
+
+def spfm_batch_step(b, n_steps, args):
+    arr = (StepArgs * len(args))(*args)
+    _check(load().spfm_batch_step(b, int(n_steps), arr))
+
+
+def spfm_batch_stats(b, n, flags=0, allow_nonfinite=False):
+    arr = (Stats * n)()
+    s = load().spfm_batch_stats(b, int(flags), arr)
+    if not (allow_nonfinite and s == SPFM_ENONFINITE):
+        _check(s)
+    return [st.as_dict() for st in arr]
+
+
+def spfm_batch_destroy(b):
+    _check(load().spfm_batch_destroy(b))
+
+
+def step_args(M=1.0, Gamma=1.0, lam=4.0, dx=1.0, dt=0.1, dF=0.0, stencil=26,
+              scheme=SPFM_TI_GLOBAL) -> StepArgs:
+    a = StepArgs()
+    a.M, a.Gamma, a.lam, a.dx, a.dt, a.dF = M, Gamma, lam, dx, dt, dF
+    a.stencil, a.scheme = int(stencil), int(scheme)
+    return a
+
+
+class Batch:
+    """Grids of one dtype stepped together (one persistent launch per step)."""
+
+    def __init__(self, grids, stream=None):
+        self.grids = list(grids)
+        handles = [g.handle for g in self.grids]
+        nbytes = spfm_batch_scratch_bytes(handles)
+        dev = self.grids[0].fields[0].device
+        self.scratch = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=dev)
+        st = stream if stream is not None else self.grids[0].stream
+        self.stream = st
+        self.handle = spfm_batch_create(handles, self.scratch.data_ptr(), self.scratch.numel(), st.cuda_stream)
+
+    def step(self, n_steps, args):
+        spfm_batch_step(self.handle, n_steps, args)
+
+    def stats(self, flags=0, allow_nonfinite=False):
+        return spfm_batch_stats(self.handle, len(self.grids), flags, allow_nonfinite)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            spfm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
