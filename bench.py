@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--n", type=int, default=512, help="grid edge")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain sweep")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
+    ap.add_argument("--serve-jobs", type=int, default=300)
+    ap.add_argument("--sweep-grids", type=int, default=256)
     return ap.parse_args()
 
 
@@ -228,6 +232,78 @@ def run_reference(args):
 # --------------------------------------------------------------------- GPU arm
 
 
+def batched_vs_plain(n_grids: int, dev):
+    """Orientation sweep: n_grids uneven grids (edges 32..96, random normals,
+    lambda/dx in {2,3,4,6}), FP32, 27-point TI with each grid's own n.  Times
+    the batched path (one persistent launch per step, graph replay) against the
+    plain path (spfm_step per grid per step) and measures each grid's velocity
+    over steps 1000..2000 of the batched run against v_th = -M dF/Gamma."""
+    import torch
+    from paper_1910_05180_gb300 import spfm as S
+    from paper_1910_05180_gb300 import workloads as WL
+    jobs = WL.orientation_sweep(n_grids=n_grids)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        grids = []
+        for j in jobs:
+            g = S.Grid(j["nx"], j["ny"], j["nz"], dtype=S.SPFM_F32, bc=(S.SPFM_CONTACT,) * 6, n=j["n"],
+                       stream=stream)
+            g.init_planar(j["c"], j["lam"])
+            grids.append(g)
+        args = [S.step_args(lam=j["lam"], dt=j["dt"], dF=j["dF"], stencil=26) for j in jobs]
+        cells = sum(j["nx"] * j["ny"] * j["nz"] for j in jobs)
+        b = S.Batch(grids, stream=stream)
+        b.step(16, args)
+        for g, a in zip(grids, args):
+            g.step(2, lam=a.lam, dt=a.dt, dF=a.dF, stencil=26)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        plain_steps, batch_steps = 10, 320
+        torch.cuda.synchronize(dev)
+        ev[0].record(stream)
+        for _ in range(plain_steps):
+            for g, a in zip(grids, args):
+                g.step(1, lam=a.lam, dt=a.dt, dF=a.dF, stencil=26)
+        ev[1].record(stream)
+        ev[2].record(stream)
+        b.step(batch_steps, args)
+        ev[3].record(stream)
+        torch.cuda.synchronize(dev)
+        plain = cells * plain_steps / (ev[0].elapsed_time(ev[1]) / 1e3)
+        batched = cells * batch_steps / (ev[2].elapsed_time(ev[3]) / 1e3)
+        # velocity accuracy on a fresh start: position after 1000 and 2000 steps
+        for g, j in zip(grids, jobs):
+            g.init_planar(j["c"], j["lam"])
+        b.step(1000, args)
+        s1 = b.stats()
+        b.step(1000, args)
+        s2 = b.stats()
+        errs = []
+        for j, a1, a2 in zip(jobs, s1, s2):
+            v = (a2["position"] - a1["position"]) / (1000 * j["dt"])
+            errs.append(abs(v / (-j["dF"]) - 1.0))
+        errs = np.array(errs)
+        b.close()
+    return {"workload": f"orientation_sweep_{n_grids}grids_f32_27pt", "cells": int(cells),
+            "plain_cell_updates_per_s": plain, "batched_cell_updates_per_s": batched,
+            "speedup": batched / plain, "velocity_rel_err_median": float(np.median(errs)),
+            "velocity_rel_err_p90": float(np.percentile(errs, 90)),
+            "velocity_rel_err_max": float(errs.max()),
+            "note": "batched and plain give bit-identical fields (tests/test_gpu_batch.py)"}
+
+
+def serving_run(n_jobs: int):
+    """Poisson stream (200 jobs/s) of velocity-measurement jobs, edges 32..192,
+    continuous batching under a 120 GB budget, retirement at |dv/v| < 1e-4."""
+    from paper_1910_05180_gb300 import workloads as WL
+    from paper_1910_05180_gb300.serve import GpuBackend, Server, job_from_workload
+    jobs = [job_from_workload(w) for w in WL.serving_stream(n_jobs=n_jobs)]
+    srv = Server(GpuBackend(), hbm_budget=120e9, window=200, tol=1e-4, max_steps=20000)
+    out = srv.run(jobs)
+    out["workload"] = f"poisson200hz_{n_jobs}jobs_edge32-192_f32_27pt"
+    return out
+
+
+
 def run_gpu(args):
     import torch
     ws, rank, local = dist_env()
@@ -275,7 +351,7 @@ def run_gpu(args):
         ev[i][0].record(stream)
         g.step(1, **kw)
         ev[i][1].record(stream)
-        launches += 1
+        launches += 2          # stencil kernel + ghost-face kernel
         if (i + 1) % STATS_EVERY == 0:
             stats_seen.append(g.stats())
             launches += 2
@@ -321,6 +397,13 @@ def run_gpu(args):
                "h2d_bytes_per_step": fb / E2E_STEPS, "d2h_bytes_per_step": (fb + 96) / E2E_STEPS,
                "note": f"per call: host field in, {E2E_STEPS} steps, stats, host field out"}
 
+    batched = None
+    if rank == 0 and not args.no_batch:
+        batched = batched_vs_plain(args.sweep_grids, dev)
+    serving = None
+    if rank == 0 and not args.no_serve:
+        serving = serving_run(args.serve_jobs)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, nzs, dt = oracle_sample(w)
@@ -343,8 +426,10 @@ def run_gpu(args):
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": profiled_traffic(kernel_key),
                          "kernel": "spfm_step_kernel", "bytes_per_update": bpu,
-                         "avg_launch_ms": avg_kernel_ms},
+                         "avg_launch_ms": avg_kernel_ms,
+                         "timed": "each step: stencil kernel + ghost-face kernel (events around both)"},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+            "batched": batched, "serving": serving,
             "last_stats": stats_seen[-1] if stats_seen else None,
         }
         print(json.dumps(line), flush=True)
