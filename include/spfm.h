@@ -138,6 +138,21 @@ spfm_status spfm_step(spfm_grid *g, int n_steps, double M, double Gamma, double 
  * NaN/Inf. */
 spfm_status spfm_interface_stats(spfm_grid *g, int flags, spfm_stats *out);
 
+/* The diagnostics above without any device allocation or caller scratch, for
+ * callers that cannot allocate device memory (their device memory belongs to
+ * another framework's pool, or they only borrow the field they measure).  The
+ * paper has no counterpart: this is a deployment variant of the stats pass.
+ * desc gives sizes, dtype, n and center (bc, buffers, scratch are not used);
+ * field is a device buffer in the ghosted layout of spfm_layout; lambda and dx
+ * define the profile inversion.  out->energy is NaN, steps and time are 0.
+ * The reduction partials sit in a fixed array inside the library, sized for
+ * nz <= 1024 (96 KiB, held by every GPU that loads the library until exit):
+ * larger nz returns SPFM_EINVAL.  The first call on a device looks up the
+ * array's address; make it before any stream capture.  Calls share the array,
+ * so calls that overlap on the GPU race.  Synchronises desc->stream. */
+spfm_status spfm_interface_stats_static(const spfm_grid_desc *desc, const void *field, double lambda,
+                                        double dx, spfm_stats *out);
+
 /* Copy the interior of the current field to/from a dense (nz, ny, nx) array of
  * the storage type; *_on_host selects a host or a device pointer.  set_field
  * resets the step count and rebuilds the ghost layer (at the next step when no

@@ -88,6 +88,7 @@ SIGNATURES = [
     ("spfm_init_sphere", _I, [_P, ctypes.POINTER(_D), _D, _D, _D]),
     ("spfm_step", _I, [_P, _I, _D, _D, _D, _D, _D, _D, _I, _I]),
     ("spfm_interface_stats", _I, [_P, _I, ctypes.POINTER(Stats)]),
+    ("spfm_interface_stats_static", _I, [ctypes.POINTER(GridDesc), _P, _D, _D, ctypes.POINTER(Stats)]),
     ("spfm_get_field", _I, [_P, _P, _I]),
     ("spfm_set_field", _I, [_P, _P, _I]),
     ("spfm_current", _I, [_P]),
@@ -166,6 +167,15 @@ def spfm_interface_stats(h, flags=0, allow_nonfinite=False) -> dict:
     s = load().spfm_interface_stats(h, int(flags), ctypes.byref(st))
     if not (allow_nonfinite and s == SPFM_ENONFINITE):
         _check(s, h)
+    return st.as_dict()
+
+
+def spfm_interface_stats_static(desc, field_ptr, lam, dx, allow_nonfinite=False) -> dict:
+    """Diagnostics of a borrowed field buffer without any device allocation."""
+    st = Stats()
+    s = load().spfm_interface_stats_static(ctypes.byref(desc), field_ptr, lam, dx, ctypes.byref(st))
+    if not (allow_nonfinite and s == SPFM_ENONFINITE):
+        _check(s)
     return st.as_dict()
 
 
