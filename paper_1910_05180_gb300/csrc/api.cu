@@ -357,8 +357,6 @@ spfm_status spfm_step(spfm_grid *g, int n_steps, double M, double Gamma, double 
     Model m;
     spfm_status st = build_model(g, M, Gamma, lambda, dx, dt, dF, stencil, scheme, m);
     if (st != SPFM_OK) return st;
-    if (scheme == SPFM_TI_LOCAL)
-        return fail(g, SPFM_EINVAL, "spfm_step: SPFM_TI_LOCAL is not available in this build");
     const LaunchCfg cfg{stencil, scheme};
     cudaStream_t s = stream_of(g);
     if (n_steps > 0 && (g->ghosts_dirty || g->ghost_lambda != lambda || g->ghost_dx != dx)) {
@@ -369,6 +367,7 @@ spfm_status spfm_step(spfm_grid *g, int n_steps, double M, double Gamma, double 
     if (g->d.dtype == SPFM_F64) {
         StepCoef<double> c;
         fill_coef<double>(g, m, dt, stencil, c);
+        set_local_coef<double>(c, lambda, dx);
         for (int i = 0; i < n_steps; ++i) {
             cudaError_t e = launch_step_f64(c, (const double *)g->d.field[g->cur],
                                             (double *)g->d.field[1 - g->cur], err, cfg, &g->tma,
@@ -381,6 +380,7 @@ spfm_status spfm_step(spfm_grid *g, int n_steps, double M, double Gamma, double 
     } else {
         StepCoef<float> c;
         fill_coef<float>(g, m, dt, stencil, c);
+        set_local_coef<float>(c, lambda, dx);
         for (int i = 0; i < n_steps; ++i) {
             cudaError_t e;
             if (g->d.dtype == SPFM_F32)

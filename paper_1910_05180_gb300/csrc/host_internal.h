@@ -83,4 +83,15 @@ void fill_coef(const spfm_grid *g, const Model &m, double dt, int stencil, spfm:
     c.nkapdt = (T)(-m.kappa * dt);
 }
 
+// TI_n constants of the step kernels: lambda/2, 1/(2 dx), 2 dx/lambda and the
+// clamp of phi before the profile inversion (1e-6)
+template <class T>
+void set_local_coef(spfm::StepCoef<T> &c, double lambda, double dx)
+{
+    c.half_lam = (T)(0.5 * lambda);
+    c.inv_2dx = (T)(1.0 / (2.0 * dx));
+    c.two_dx_over_lam = (T)(2.0 * dx / lambda);
+    c.eps = (T)1e-6;
+}
+
 }  // namespace spfm_host

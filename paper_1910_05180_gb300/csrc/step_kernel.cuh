@@ -269,11 +269,11 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
 #define SPFM_ROWS_PER_THREAD 2
 #endif
 
-template <class S, class T, int TX, int TY>
+template <class S, class T, int TX, int TY, int RPT_ = SPFM_ROWS_PER_THREAD>
 struct TileShape {
     static constexpr int VX = Io<S, T>::VX;
     static constexpr int NP = VX / 2;
-    static constexpr int RPT = SPFM_ROWS_PER_THREAD;   // rows of the tile per consumer thread
+    static constexpr int RPT = RPT_;   // rows of the tile per consumer thread
     static constexpr int W = TX * VX;
     static constexpr int SW = W + 2 * VX;   // staged row: one 16-byte chunk of halo per side
     static constexpr int ROWS = TY + 2;
@@ -290,7 +290,74 @@ template <class T, int NP>
 struct PlaneQ {
     using P = typename Pk<T>::P;
     P c[NP], h[NP], g[NP];
+    P psi[NP], gx[NP], gy[NP];   // TI_n only: profile inversion and its in-plane differences
 };
+
+// ----------------------------------------------------------------- TI_n
+
+// Inversion of the ideal profile, psi = (lambda/2) artanh(1 - 2 phi)
+// = (lambda/4) ln((1 - phi)/phi), with phi clamped to [eps, 1 - eps] (TI_n).
+__device__ __forceinline__ float psi_of(float phi, float quarter_lam, float eps)
+{
+    const float pc = fminf(fmaxf(phi, eps), 1.0f - eps);
+    return quarter_lam * __logf(__fdividef(1.0f - pc, pc));
+}
+__device__ __forceinline__ double psi_of(double phi, double quarter_lam, double eps)
+{
+    const double pc = fmin(fmax(phi, eps), 1.0 - eps);
+    return quarter_lam * log((1.0 - pc) / pc);
+}
+template <class T>
+__device__ __forceinline__ typename Pk<T>::P psi_pack(typename Pk<T>::P v, T quarter_lam, T eps)
+{
+    return Pk<T>::mk(psi_of(v.x, quarter_lam, eps), psi_of(v.y, quarter_lam, eps));
+}
+__device__ __forceinline__ float tanh_of(float x) { return tanhf(x); }
+__device__ __forceinline__ double tanh_of(double x) { return tanh(x); }
+
+// TI_n factor w = -dt (potential / q + 4 M dF / (lambda Gamma)) of one cell with
+// phi, s = 1 - 2 phi, u = s^2 and the profile-inversion gradient g (Sec. 2.1,
+// TI_n): n = g / |g|, t_i = tanh(2 dx n_i / lambda), the 13 couplings from the
+// tanh addition theorem (a = N / D), and the potential sum
+// sum_k 4 c_k a_k^2 / (1 - a_k^2 s^2) = sum_k 4 c_k N^2 / (D^2 - N^2 s^2).
+// Where |g| < 1e-8 the normal is undefined and the cell takes the CF potential.
+template <class T>
+__device__ __forceinline__ T ti_local_w(const StepCoef<T> &C, T s, T u, T gx, T gy, T gz)
+{
+    const T g2 = gx * gx + gy * gy + gz * gz;
+    if (!(g2 >= T(1e-16))) return s * (-C.dt * C.kappa) - C.dt * C.kmu;
+    const T inv = T(1) / sqrt(g2);
+    const T k2 = C.two_dx_over_lam;
+    const T tx = tanh_of(k2 * gx * inv), ty = tanh_of(k2 * gy * inv), tz = tanh_of(k2 * gz * inv);
+    T sum = T(0);
+    auto term = [&](T ck, T N, T D) {
+        const T N2 = N * N;
+        sum += T(4) * ck * N2 / (D * D - N2 * u);
+    };
+    // shell 1: (1,0,0), (0,1,0), (0,0,1)
+    term(C.ck[0], tx, T(1));
+    term(C.ck[1], ty, T(1));
+    term(C.ck[2], tz, T(1));
+    if (C.ck[3] != T(0)) {
+        // shell 2: (1,1,0), (0,1,1), (1,0,1), (1,-1,0), (0,1,-1), (1,0,-1)
+        term(C.ck[3], tx + ty, T(1) + tx * ty);
+        term(C.ck[4], ty + tz, T(1) + ty * tz);
+        term(C.ck[5], tx + tz, T(1) + tx * tz);
+        term(C.ck[6], tx - ty, T(1) - tx * ty);
+        term(C.ck[7], ty - tz, T(1) - ty * tz);
+        term(C.ck[8], tx - tz, T(1) - tx * tz);
+    }
+    if (C.ck[9] != T(0)) {
+        // shell 3: (1,1,1), (-1,1,1), (1,-1,1), (1,1,-1):
+        // tanh(a + b + c) = (ta + tb + tc + ta tb tc) / (1 + ta tb + tb tc + ta tc)
+        auto t3 = [&](T a, T b, T c) { term(C.ck[9], a + b + c + a * b * c, T(1) + a * b + b * c + a * c); };
+        t3(tx, ty, tz);
+        t3(-tx, ty, tz);
+        t3(tx, -ty, tz);
+        t3(tx, ty, -tz);
+    }
+    return s * (-C.dt * sum) - C.dt * C.kmu;
+}
 
 // The packs of one staged row around a thread's cells (adjacent pairs):
 // c[p] = (x+2p, x+2p+1), w[p] = c shifted by -1, e[p] = shifted by +1.
@@ -317,19 +384,20 @@ __device__ __forceinline__ void get_row(const S *r, typename Pk<T>::P *c, typena
 // tiles a CTA processes: plane i of this tile is ring slot base + i.  The
 // producer waits for its copies in flight before returning when drain is set.
 // Returns false when a bounded wait gave up (the error word is set).
-template <class S, class T, int STENCIL, int KIND, int TX, int TY>
+template <class S, class T, int STENCIL, int KIND, int TX, int TY, int RPT_>
 __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T> &PC,
                                           const S *__restrict__ src, S *__restrict__ dst,
                                           int *__restrict__ err, const CUtensorMap *tmap, int bx,
                                           int by, int zc0, int zc1, S *__restrict__ stages,
                                           uint64_t *full, uint64_t *empty, int base, bool drain)
 {
-    using Sh = TileShape<S, T, TX, TY>;
+    using Sh = TileShape<S, T, TX, TY, RPT_>;
     using K = Pk<T>;
     using P = typename K::P;
     constexpr int VX = Sh::VX, NP = Sh::NP, W = Sh::W, SW = Sh::SW, ROWS = Sh::ROWS;
     constexpr int STAGE = Sh::STAGE, NS = Sh::NS;
     constexpr int NTMAX = KIND >= 1 && KIND <= 4 ? KIND : kMaxTerms;
+    static_assert(KIND != 6 || RPT_ == 1, "TI_n runs one row per thread");
 
     const GridGeom &g = C.g;
     const int tid = threadIdx.x;
@@ -415,6 +483,16 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
                         p[r].g[q] = STENCIL == 26 ? K::fma(PC.c3, e, K::mul(PC.c2, f)) : K::mul(PC.c2, f);
                     }
                 }
+                if (KIND == 6) {
+                    // psi at the cells and central differences along x and y
+                    const T ql = C.half_lam * T(0.5), ep = C.eps;
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) {
+                        p[r].psi[q] = psi_pack<T>(rc[r + 1][q], ql, ep);
+                        p[r].gx[q] = K::sub(psi_pack<T>(re[r + 1][q], ql, ep), psi_pack<T>(rw[r + 1][q], ql, ep));
+                        p[r].gy[q] = K::sub(psi_pack<T>(rc[r + 2][q], ql, ep), psi_pack<T>(rc[r][q], ql, ep));
+                    }
+                }
             }
         }
         if (i >= 2) {
@@ -434,6 +512,12 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
                     P w;   // -dt (potential / q + 4 M dF / (lambda Gamma))
                     if (KIND == 0) {
                         w = K::fma(sg, PC.nkap, PC.nkmu);
+                    } else if (KIND == 6) {
+                        const P u = K::mul(sg, sg);
+                        const P gz = K::sub(p[r].psi[q], m[r].psi[q]);
+                        const T s2 = C.inv_2dx;
+                        w = K::mk(ti_local_w<T>(C, sg.x, u.x, z[r].gx[q].x * s2, z[r].gy[q].x * s2, gz.x * s2),
+                                  ti_local_w<T>(C, sg.y, u.y, z[r].gx[q].y * s2, z[r].gy[q].y * s2, gz.y * s2));
                     } else {
                         const P u = K::mul(sg, sg);
                         P num = PC.nbeta[0];
@@ -477,13 +561,13 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
 // minimum resident CTAs per SM (two 288-thread CTAs leave 113 registers a thread)
 template <class S> struct MinBlocks { static constexpr int value = SPFM_MIN_CTAS; };
 
-template <class S, class T, int STENCIL, int KIND, int TX, int TY>
-__global__ void __launch_bounds__(TileShape<S, T, TX, TY>::NTHREADS, MinBlocks<S>::value)
+template <class S, class T, int STENCIL, int KIND, int TX, int TY, int RPT_>
+__global__ void __launch_bounds__(TileShape<S, T, TX, TY, RPT_>::NTHREADS, RPT_ == 1 ? 2 : MinBlocks<S>::value)
     spfm_step_kernel(const StepCoef<T> C, const PackCoef<T> PC, const S *__restrict__ src,
                      S *__restrict__ dst, int *__restrict__ err, int zchunk,
                      const __grid_constant__ CUtensorMap tmap, int use_tmap)
 {
-    using Sh = TileShape<S, T, TX, TY>;
+    using Sh = TileShape<S, T, TX, TY, RPT_>;
     __shared__ __align__(128) S stages[Sh::NS * Sh::STAGE];
     __shared__ __align__(8) uint64_t full[Sh::NS], empty[Sh::NS];
     if (threadIdx.x == 0) {
@@ -496,9 +580,9 @@ __global__ void __launch_bounds__(TileShape<S, T, TX, TY>::NTHREADS, MinBlocks<S
     __syncthreads();
     const int zc0 = blockIdx.z * zchunk;
     const int zc1 = min(zc0 + zchunk, C.g.nz);
-    step_tile<S, T, STENCIL, KIND, TX, TY>(C, PC, src, dst, err, use_tmap ? &tmap : nullptr,
-                                           blockIdx.x, blockIdx.y, zc0, zc1, stages, full, empty, 0,
-                                           true);
+    step_tile<S, T, STENCIL, KIND, TX, TY, RPT_>(C, PC, src, dst, err, use_tmap ? &tmap : nullptr,
+                                                 blockIdx.x, blockIdx.y, zc0, zc1, stages, full, empty, 0,
+                                                 true);
 }
 
 // ------------------------------------------------------------------- batches
@@ -541,7 +625,7 @@ __global__ void __launch_bounds__(TileShape<S, T, TX, TY>::NTHREADS, MinBlocks<S
         if (map && threadIdx.x == Sh::NCONS)
             asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
         const bool last = w + (int)gridDim.x >= nwork;
-        if (!step_tile<S, T, STENCIL, KIND, TX, TY>(bg.C, bg.PC, (const S *)bg.field[cur],
+        if (!step_tile<S, T, STENCIL, KIND, TX, TY, SPFM_ROWS_PER_THREAD>(bg.C, bg.PC, (const S *)bg.field[cur],
                                                     (S *)bg.field[cur ^ 1], err, map, it.bx, it.by,
                                                     it.zc0, it.zc1, stages, full, empty, base, last))
             return;
@@ -613,15 +697,19 @@ cudaError_t launch_step_t(const StepCoef<T> &c, const S *src, S *dst, int *err, 
     const dim3 grid(gxn, gyn, (c.g.nz + zchunk - 1) / zchunk);
     // exact group counts 1..4 get their own kernels; 0 groups (all A_k = 0)
     // runs the one-group kernel with beta = 0
-    const int kind = cfg.scheme == SPFM_FD ? 0 : (c.nterms <= 4 ? (c.nterms < 1 ? 1 : c.nterms) : 5);
+    const int kind = cfg.scheme == SPFM_FD ? 0
+                     : cfg.scheme == SPFM_TI_LOCAL ? 6
+                                                   : (c.nterms <= 4 ? (c.nterms < 1 ? 1 : c.nterms) : 5);
     const PackCoef<T> pc = make_pack_coef<T>(c);
     CUtensorMap map;
     if (tmap) map = *tmap;
     else memset(&map, 0, sizeof map);
     const int use = tmap ? 1 : 0;
-#define SPFM_LAUNCH(ST, KD)                                                                   \
-    spfm_step_kernel<S, T, ST, KD, TX, TY><<<grid, Sh::NTHREADS, 0, st>>>(c, pc, src, dst, err, \
-                                                                          zchunk, map, use)
+    constexpr int R = SPFM_ROWS_PER_THREAD;
+    constexpr int NT1 = TileShape<S, T, TX, TY, 1>::NTHREADS;
+#define SPFM_LAUNCH(ST, KD)                                                                      \
+    spfm_step_kernel<S, T, ST, KD, TX, TY, R><<<grid, Sh::NTHREADS, 0, st>>>(c, pc, src, dst, err, \
+                                                                             zchunk, map, use)
 #define SPFM_BY_KIND(ST)                        \
     do {                                        \
         if (kind == 0) SPFM_LAUNCH(ST, 0);      \
@@ -629,7 +717,8 @@ cudaError_t launch_step_t(const StepCoef<T> &c, const S *src, S *dst, int *err, 
         else if (kind == 2) SPFM_LAUNCH(ST, 2); \
         else if (kind == 3) SPFM_LAUNCH(ST, 3); \
         else if (kind == 4) SPFM_LAUNCH(ST, 4); \
-        else SPFM_LAUNCH(ST, 5);                \
+        else if (kind == 5) SPFM_LAUNCH(ST, 5); \
+        else spfm_step_kernel<S, T, ST, 6, TX, TY, 1><<<grid, NT1, 0, st>>>(c, pc, src, dst, err, zchunk, map, use); \
     } while (0)
     if (cfg.stencil == 6) SPFM_BY_KIND(6);
     else if (cfg.stencil == 18) SPFM_BY_KIND(18);

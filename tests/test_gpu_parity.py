@@ -225,3 +225,37 @@ def test_tilted_256cubed_sampled_cone_parity(dtype):
     kw = dict(n=w["n"], lam=w["lam"], dt=w["dt"], dF=w["dF"], stencil=26, scheme=O.TI_GLOBAL)
     errs = [abs(out[s] - cone_reference(start, (N, N, N), bc, s, T, kw)) for s in pts]
     assert max(errs) <= TOL[dtype], max(errs)
+
+
+# ------------------------------------------------------------------ TI_n
+
+
+@pytest.mark.parametrize("dtype", [S.SPFM_F64, S.SPFM_F32])
+@pytest.mark.parametrize("stencil", [26, 18, 6])
+def test_ti_local_normal_sphere_parity(dtype, stencil):
+    """TI_n on a curved interface (grain of radius 11, periodic 44x40x36) against
+    the oracle's TI_n (local normal from the profile inversion)."""
+    shape = (44, 40, 36)
+    g, p = make_pair(*shape, dtype, (S.SPFM_PERIODIC,) * 6, (1.0, 0.0, 0.0), lam=3.0, dt=0.05,
+                     dF=0.02, stencil=stencil, scheme=S.SPFM_TI_LOCAL)
+    ctr = (21.3, 19.6, 17.2)
+    phi0 = O.init_sphere(p, ctr, 11.0)
+    start = upload(g, phi0, dtype)
+    g.step(30, lam=3.0, dt=0.05, dF=0.02, stencil=stencil, scheme=S.SPFM_TI_LOCAL)
+    ref = O.step(p, start, 30)
+    err = np.abs(gpu_field(g) - ref).max()
+    assert err <= TOL[dtype], err
+
+
+@pytest.mark.parametrize("dtype", [S.SPFM_F64, S.SPFM_F32])
+def test_ti_local_normal_tilted_plane_parity(dtype):
+    n = rng_normal(44)
+    shape = (37, 21, 19)
+    g, p = make_pair(*shape, dtype, (S.SPFM_CONTACT,) * 6, n, lam=2.5, dt=0.05, dF=0.03, stencil=26,
+                     scheme=S.SPFM_TI_LOCAL)
+    rng = np.random.default_rng(45)
+    phi0 = O.init_planar(p, float(n @ (np.array(shape) - 1) / 2.0)) + 0.005 * rng.random(p.shape)
+    start = upload(g, phi0, dtype)
+    g.step(25, lam=2.5, dt=0.05, dF=0.03, stencil=26, scheme=S.SPFM_TI_LOCAL)
+    ref = O.step(p, start, 25)
+    assert np.abs(gpu_field(g) - ref).max() <= TOL[dtype]
