@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64", "bf16"])
-    ap.add_argument("--scheme", default="ti120", choices=["ti120", "fd"])
+    ap.add_argument("--scheme", default="ti120", choices=["ti120", "fd", "local"])
+    ap.add_argument("--no-variants", action="store_true", help="skip the TI_n / CF timings")
     ap.add_argument("--n", type=int, default=512, help="grid edge")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -317,7 +318,7 @@ def run_gpu(args):
 
     w = workload(args)
     dtype = {"f32": S.SPFM_F32, "f64": S.SPFM_F64, "bf16": S.SPFM_BF16}[args.dtype]
-    scheme = {"ti120": S.SPFM_TI_GLOBAL, "fd": S.SPFM_FD}[args.scheme]
+    scheme = {"ti120": S.SPFM_TI_GLOBAL, "fd": S.SPFM_FD, "local": S.SPFM_TI_LOCAL}[args.scheme]
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         g = S.Grid(w["nx"], w["ny"], w["nz"], dtype=dtype, bc=(S.SPFM_PERIODIC,) * 6, n=w["u"],
@@ -372,6 +373,30 @@ def run_gpu(args):
     achieved = cells * bpu / (avg_kernel_ms / 1e3) / 1e9
     kernel_key = f"spfm_step_kernel_{args.dtype}_27pt_{args.scheme}_{w['nx']}"
 
+    # grain anisotropy after the timed run (Sec. 3.3), FP64 on the device
+    grain = g.sphericity(0) if rank == 0 else None
+
+    # the other schemes on the same grid and storage (short timed runs)
+    variants = None
+    if rank == 0 and not args.no_variants:
+        variants = {}
+        for name, sch in (("TI_n", S.SPFM_TI_LOCAL), ("CF+h3", S.SPFM_FD), ("TI_<120>", S.SPFM_TI_GLOBAL)):
+            if sch == scheme:
+                continue
+            kw2 = dict(kw, scheme=sch)
+            g.init_sphere(w["ctr"], w["R"], w["lam"], w["dx"])
+            g.step(5, **kw2)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            nvar = 100
+            barrier()
+            e0.record(stream)
+            g.step(nvar, **kw2)
+            e1.record(stream)
+            barrier()
+            ms = e0.elapsed_time(e1) / nvar
+            variants[name] = {"cell_updates_per_s": cells / (ms / 1e3), "ms_per_step": ms,
+                              "frac_hbm": cells * bpu / (ms / 1e3) / 1e9 / peak}
+
     # end to end through the public API from pinned host memory: upload the
     # initial field, E2E_STEPS steps, stats, read the field back
     e2e = None
@@ -417,7 +442,7 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": w["name"] + f"_{args.scheme}_{args.dtype}_27pt",
                        "grid": [w["nx"], w["ny"], w["nz"]], "stencil": 27,
-                       "scheme": "TI_<120>" if args.scheme == "ti120" else "CF+h3",
+                       "scheme": {"ti120": "TI_<120>", "fd": "CF+h3", "local": "TI_n"}[args.scheme],
                        "lambda": w["lam"], "dt": w["dt"], "dF": w["dF"], "bc": "periodic",
                        "stats_every": STATS_EVERY,
                        "l2": "inputs larger than L2 (two %d MB fields)" % (cells * bpu // 2 // 2**20),
@@ -429,7 +454,7 @@ def run_gpu(args):
                          "avg_launch_ms": avg_kernel_ms,
                          "timed": "each step: stencil kernel + ghost-face kernel (events around both)"},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
-            "batched": batched, "serving": serving,
+            "batched": batched, "serving": serving, "grain_sphericity": grain, "variants": variants,
             "last_stats": stats_seen[-1] if stats_seen else None,
         }
         print(json.dumps(line), flush=True)

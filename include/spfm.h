@@ -153,6 +153,15 @@ spfm_status spfm_interface_stats(spfm_grid *g, int flags, spfm_stats *out);
 spfm_status spfm_interface_stats_static(const spfm_grid_desc *desc, const void *field, double lambda,
                                         double dx, spfm_stats *out);
 
+/* Residual anisotropy of a particle (Sec. 3.3): the phi = 1/2 contour points on
+ * the grid edges (nonlinear interpolation of Sec. 2.3, Eqs. 8-10), their
+ * distances R_i from the particle's barycentre (cells weighted by their
+ * particle-phase fraction; the particle is phase inside_phase, 0 or 1), and
+ * out[0] eps_eff = (R_max - R_min)/(2 R_mean), out[1] R_mean, out[2] R_min,
+ * out[3] R_max, out[4] number of contour points, out[5..7] barycentre.  FP64,
+ * uses the grid's scratch, synchronises the stream. */
+spfm_status spfm_sphericity(spfm_grid *g, int inside_phase, double *out8);
+
 /* Copy the interior of the current field to/from a dense (nz, ny, nx) array of
  * the storage type; *_on_host selects a host or a device pointer.  set_field
  * resets the step count and rebuilds the ghost layer (at the next step when no

@@ -89,6 +89,7 @@ SIGNATURES = [
     ("spfm_step", _I, [_P, _I, _D, _D, _D, _D, _D, _D, _I, _I]),
     ("spfm_interface_stats", _I, [_P, _I, ctypes.POINTER(Stats)]),
     ("spfm_interface_stats_static", _I, [ctypes.POINTER(GridDesc), _P, _D, _D, ctypes.POINTER(Stats)]),
+    ("spfm_sphericity", _I, [_P, _I, ctypes.POINTER(_D)]),
     ("spfm_get_field", _I, [_P, _P, _I]),
     ("spfm_set_field", _I, [_P, _P, _I]),
     ("spfm_current", _I, [_P]),
@@ -179,6 +180,13 @@ def spfm_interface_stats_static(desc, field_ptr, lam, dx, allow_nonfinite=False)
     return st.as_dict()
 
 
+def spfm_sphericity(h, inside_phase=0) -> dict:
+    out = (ctypes.c_double * 8)()
+    _check(load().spfm_sphericity(h, int(inside_phase), out), h)
+    return {"eps_eff": out[0], "R_mean": out[1], "R_min": out[2], "R_max": out[3],
+            "n_points": int(out[4]), "barycentre": [out[5], out[6], out[7]]}
+
+
 def spfm_get_field(h, ptr, on_host):
     _check(load().spfm_get_field(h, ptr, int(on_host)), h)
 
@@ -253,6 +261,9 @@ class Grid:
 
     def stats(self, flags=0, allow_nonfinite=False) -> dict:
         return spfm_interface_stats(self.handle, flags, allow_nonfinite)
+
+    def sphericity(self, inside_phase=0) -> dict:
+        return spfm_sphericity(self.handle, inside_phase)
 
     def current(self) -> torch.Tensor:
         """View (nz, ny, nx) of the interior of the buffer holding the current field."""

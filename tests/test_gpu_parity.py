@@ -259,3 +259,24 @@ def test_ti_local_normal_tilted_plane_parity(dtype):
     g.step(25, lam=2.5, dt=0.05, dF=0.03, stencil=26, scheme=S.SPFM_TI_LOCAL)
     ref = O.step(p, start, 25)
     assert np.abs(gpu_field(g) - ref).max() <= TOL[dtype]
+
+
+# ------------------------------------------------------------ sphericity
+
+
+@pytest.mark.parametrize("dtype", [S.SPFM_F64, S.SPFM_F32])
+def test_sphericity_matches_oracle(dtype):
+    """Sec. 3.3 eps_eff from the nonlinear contour points, after TI_n relaxation."""
+    shape = (40, 36, 32)
+    g, p = make_pair(*shape, dtype, (S.SPFM_PERIODIC,) * 6, (1.0, 0.0, 0.0), lam=3.0, dt=0.05,
+                     dF=0.0, stencil=26, scheme=S.SPFM_TI_LOCAL)
+    phi0 = O.init_sphere(p, (19.4, 17.8, 15.3), 9.5)
+    start = upload(g, phi0, dtype)
+    g.step(20, lam=3.0, dt=0.05, dF=0.0, stencil=26, scheme=S.SPFM_TI_LOCAL)
+    field = gpu_field(g)
+    got = g.sphericity(0)
+    ref = O.sphericity(p, field, inside_phase=0)
+    assert got["n_points"] == ref["n_points"]
+    for k in ("eps_eff", "R_mean", "R_min", "R_max"):
+        assert abs(got[k] - ref[k]) <= 1e-11 * max(1.0, abs(ref[k])), (k, got[k], ref[k])
+    assert np.allclose(got["barycentre"], ref["barycentre"], rtol=0, atol=1e-10)
