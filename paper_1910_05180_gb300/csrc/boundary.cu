@@ -72,6 +72,9 @@ __device__ __forceinline__ void ghost_faces(const FaceArgs &a, S *f, long long t
 template <class S>
 __global__ void __launch_bounds__(256) ghost_kernel(const FaceArgs a, S *f)
 {
+    // the next step kernel may launch now: its boxes that touch a face wait for
+    // this grid to complete (griddepcontrol.wait), the others read no ghost
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     ghost_faces<S>(a, f, blockIdx.x * (long long)blockDim.x + threadIdx.x,
                    (long long)gridDim.x * blockDim.x);
 }

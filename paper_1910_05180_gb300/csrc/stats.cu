@@ -116,29 +116,45 @@ __device__ __forceinline__ void block_reduce_store(double *v, double *out)
 
 // Per-thread partials: [0] sum phi, [1] S_w, [2] S_c, [3] S_r, [4] min, [5] max,
 // [6] non-finite count, [7] energy density sum, [8..11] unused.
+// Screening type of a storage type: comparisons (finite, min, max, band) are
+// exact in the storage precision, so only the sums run in FP64.
+template <class S> struct Scr { using T = float; };
+template <> struct Scr<double> { using T = double; };
+template <class S> __device__ __forceinline__ typename Scr<S>::T scr(const S *f, long long i);
+template <> __device__ __forceinline__ double scr<double>(const double *f, long long i) { return f[i]; }
+template <> __device__ __forceinline__ float scr<float>(const float *f, long long i) { return f[i]; }
+template <> __device__ __forceinline__ float scr<__nv_bfloat16>(const __nv_bfloat16 *f, long long i)
+{
+    return __bfloat162float(f[i]);
+}
+
+// Partial sums of one block over its contiguous range of rows: block b of nb
+// takes rows [b * rows / nb, (b + 1) * rows / nb), rows ordered (j fastest, k).
 template <class S>
 __device__ __forceinline__ void stats_pass(const StatsArgs &a, const S *f, double *partial_out,
-                                           long long row0, long long row_stride)
+                                           long long blk, long long nblk)
 {
+    using R = typename Scr<S>::T;
     double v[kNStat];
 #pragma unroll
     for (int i = 0; i < kNStat; ++i) v[i] = 0.0;
-    v[4] = INFINITY;
-    v[5] = -INFINITY;
+    R mn = R(INFINITY), mx = R(-INFINITY);
     const double e_pref = a.Gamma / (a.C_gamma * a.lambda);
     const int nd = a.stencil == 6 ? 3 : (a.stencil == 18 ? 9 : 13);
+    const R lo = R(0.5e-6), hi = R(1.0 - 0.5e-6);   // conservative pre-filter of the FP64 band test
     const long long rows = (long long)a.g.ny * a.g.nz;
-    for (long long row = row0; row < rows; row += row_stride) {
-        const int j = (int)(row % a.g.ny);
-        const int k = (int)(row / a.g.ny);
+    const long long r0 = blk * rows / nblk, r1 = (blk + 1) * rows / nblk;
+    int j = (int)(r0 % a.g.ny), k = (int)(r0 / a.g.ny);
+    for (long long row = r0; row < r1; ++row) {
         const long long rbase = cell_index(a.g, 0, j, k);
         for (int i = threadIdx.x; i < a.g.nx; i += blockDim.x) {
-            const double ph = rd<S>(f, rbase + i);
-            if (!isfinite(ph)) { v[6] += 1.0; continue; }
+            const R r = scr<S>(f, rbase + i);
+            if (!isfinite(r)) { v[6] += 1.0; continue; }
+            const double ph = (double)r;   // exact
             v[0] += ph;
-            v[4] = fmin(v[4], ph);
-            v[5] = fmax(v[5], ph);
-            if (ph > 1e-6 && ph < 1.0 - 1e-6) {
+            mn = r < mn ? r : mn;
+            mx = r > mx ? r : mx;
+            if (r > lo && r < hi && ph > 1e-6 && ph < 1.0 - 1e-6) {
                 const double q = ph * (1.0 - ph);
                 const double psi = 0.5 * a.lambda * atanh(1.0 - 2.0 * ph);
                 const double px = a.dx * i, py = a.dx * j, pz = a.dx * k;
@@ -161,7 +177,10 @@ __device__ __forceinline__ void stats_pass(const StatsArgs &a, const S *f, doubl
                 v[7] += e_pref * e;
             }
         }
+        if (++j == a.g.ny) { j = 0; ++k; }
     }
+    v[4] = (double)mn;
+    v[5] = (double)mx;
     block_reduce_store(v, partial_out);
 }
 

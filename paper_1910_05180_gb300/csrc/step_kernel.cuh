@@ -389,7 +389,8 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
                                           const S *__restrict__ src, S *__restrict__ dst,
                                           int *__restrict__ err, const CUtensorMap *tmap, int bx,
                                           int by, int zc0, int zc1, S *__restrict__ stages,
-                                          uint64_t *full, uint64_t *empty, int base, bool drain)
+                                          uint64_t *full, uint64_t *empty, int base, bool drain,
+                                          bool wait_prior = false)
 {
     using Sh = TileShape<S, T, TX, TY, RPT_>;
     using K = Pk<T>;
@@ -407,6 +408,12 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
     if (tid >= Sh::NCONS) {
         // ------------------------------------------------------- producer warp
         if (tid != Sh::NCONS) return true;
+        // The kernel may start while the previous launch (the ghost-face refresh
+        // of src) still runs (programmatic dependent launch).  A box that holds
+        // no ghost cell reads only interior cells, which the step before that
+        // wrote; a box touching a face waits for the previous grid first.
+        if (wait_prior && (bx == 0 || x0 + W >= g.nx || by == 0 || y0 + TY >= g.ny || zc0 == 0 || zc1 == g.nz))
+            asm volatile("griddepcontrol.wait;" ::: "memory");
         int issued = 0;
         bool ok = true;
         for (int i = 0; i < nplanes; ++i) {
@@ -565,7 +572,7 @@ template <class S, class T, int STENCIL, int KIND, int TX, int TY, int RPT_>
 __global__ void __launch_bounds__(TileShape<S, T, TX, TY, RPT_>::NTHREADS, RPT_ == 1 ? 2 : MinBlocks<S>::value)
     spfm_step_kernel(const StepCoef<T> C, const PackCoef<T> PC, const S *__restrict__ src,
                      S *__restrict__ dst, int *__restrict__ err, int zchunk,
-                     const __grid_constant__ CUtensorMap tmap, int use_tmap)
+                     const __grid_constant__ CUtensorMap tmap, int use_tmap, int pdl)
 {
     using Sh = TileShape<S, T, TX, TY, RPT_>;
     __shared__ __align__(128) S stages[Sh::NS * Sh::STAGE];
@@ -582,7 +589,7 @@ __global__ void __launch_bounds__(TileShape<S, T, TX, TY, RPT_>::NTHREADS, RPT_ 
     const int zc1 = min(zc0 + zchunk, C.g.nz);
     step_tile<S, T, STENCIL, KIND, TX, TY, RPT_>(C, PC, src, dst, err, use_tmap ? &tmap : nullptr,
                                                  blockIdx.x, blockIdx.y, zc0, zc1, stages, full, empty, 0,
-                                                 true);
+                                                 true, pdl != 0);
 }
 
 // ------------------------------------------------------------------- batches
@@ -707,9 +714,24 @@ cudaError_t launch_step_t(const StepCoef<T> &c, const S *src, S *dst, int *err, 
     const int use = tmap ? 1 : 0;
     constexpr int R = SPFM_ROWS_PER_THREAD;
     constexpr int NT1 = TileShape<S, T, TX, TY, 1>::NTHREADS;
-#define SPFM_LAUNCH(ST, KD)                                                                      \
-    spfm_step_kernel<S, T, ST, KD, TX, TY, R><<<grid, Sh::NTHREADS, 0, st>>>(c, pc, src, dst, err, \
-                                                                             zchunk, map, use)
+    // programmatic dependent launch: the kernel may begin while the previous
+    // kernel in the stream runs; boxes touching a face wait (griddepcontrol)
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = grid;
+    lc.dynamicSmemBytes = 0;
+    lc.stream = st;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    const int pdl = 1;
+    auto go = [&](auto kern, int threads) {
+        lc.blockDim = dim3(threads);
+        return cudaLaunchKernelEx(&lc, kern, c, pc, src, dst, err, zchunk, map, use, pdl);
+    };
+    cudaError_t le = cudaSuccess;
+#define SPFM_LAUNCH(ST, KD) le = go(spfm_step_kernel<S, T, ST, KD, TX, TY, R>, Sh::NTHREADS)
 #define SPFM_BY_KIND(ST)                        \
     do {                                        \
         if (kind == 0) SPFM_LAUNCH(ST, 0);      \
@@ -718,13 +740,14 @@ cudaError_t launch_step_t(const StepCoef<T> &c, const S *src, S *dst, int *err, 
         else if (kind == 3) SPFM_LAUNCH(ST, 3); \
         else if (kind == 4) SPFM_LAUNCH(ST, 4); \
         else if (kind == 5) SPFM_LAUNCH(ST, 5); \
-        else spfm_step_kernel<S, T, ST, 6, TX, TY, 1><<<grid, NT1, 0, st>>>(c, pc, src, dst, err, zchunk, map, use); \
+        else le = go(spfm_step_kernel<S, T, ST, 6, TX, TY, 1>, NT1); \
     } while (0)
     if (cfg.stencil == 6) SPFM_BY_KIND(6);
     else if (cfg.stencil == 18) SPFM_BY_KIND(18);
     else SPFM_BY_KIND(26);
 #undef SPFM_BY_KIND
 #undef SPFM_LAUNCH
+    if (le != cudaSuccess) return le;
     return cudaGetLastError();
 }
 
