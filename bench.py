@@ -463,6 +463,8 @@ def run_gpu(args):
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
             "batched": batched, "serving": serving, "grain_sphericity": grain, "variants": variants,
             "last_stats": stats_seen[-1] if stats_seen else None,
+            "stats_call": {"ms": (total_ms - step_ms) / max(1, len(stats_seen)), "every": STATS_EVERY,
+                           "note": "interface stats between step chunks, host round trip included"},
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

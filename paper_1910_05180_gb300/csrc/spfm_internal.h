@@ -15,7 +15,7 @@
 namespace spfm {
 
 constexpr int kMaxTerms = 13;    // grid directions of the 26-neighbour stencil (Tab. 1)
-constexpr int kStatsBlocks = 608;  // 4 x 152 SMs; fixed so the reduction order is fixed
+constexpr int kStatsBlocks = 608;  // most stats partials; a launch takes one full wave of at most this
 constexpr int kNStat = 12;       // doubles per partial (see stats.cu)
 
 // Grid vectors of Tab. 1, one per +/- pair: shell 1 (k = 0..2), shell 2

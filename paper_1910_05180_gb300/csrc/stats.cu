@@ -4,8 +4,8 @@
 // init: Eq. 3 (planar) or its radial form, evaluated in FP64 per cell and
 // rounded once to the storage type (the caller then fills the ghost layer).
 //
-// stats: one pass over the interior accumulating in FP64, per thread in a
-// fixed row order, then warp-shuffle and shared-memory block reductions into
+// stats: one pass over the interior with FP64 sums, per lane in a fixed
+// order, then warp-shuffle and shared-memory block reductions into
 // kStatsBlocks partials, then one CTA reducing the partials in a fixed order,
 // so the result is bit-reproducible for a given grid size.  Sums over the band
 // 1e-6 < phi < 1 - 1e-6 invert the ideal profile (Sec. 2.3):
@@ -14,6 +14,8 @@
 // The optional interface energy is Eq. 1 at dF = 0; its forward differences
 // read the ghost layer.
 #include <math.h>
+
+#include <mutex>
 
 #include "spfm_internal.h"
 
@@ -114,10 +116,19 @@ __device__ __forceinline__ void block_reduce_store(double *v, double *out)
     }
 }
 
-// Per-thread partials: [0] sum phi, [1] S_w, [2] S_c, [3] S_r, [4] min, [5] max,
+// Per-lane partials: [0] sum phi, [1] S_w, [2] S_c, [3] S_r, [4] min, [5] max,
 // [6] non-finite count, [7] energy density sum, [8..11] unused.
-// Screening type of a storage type: comparisons (finite, min, max, band) are
-// exact in the storage precision, so only the sums run in FP64.
+//
+// The pass is bound by the FP64 work of the band cells (GB300 issues FP64 at
+// 1/64 of the FP32 rate), so everything else stays out of FP64:
+//   - each warp walks whole rows with 16-byte loads; finiteness, min, max and
+//     the band test run in the storage precision, where they are exact (the
+//     band limits 1e-6 and 1 - 1e-6 are not floats, so the first float above
+//     and the last float below them decide exactly the same cells);
+//   - an FP32 field's volume is summed per lane and row as an unevaluated pair
+//     (TwoSum, Knuth TAOCP vol. 2, 4.2.2), carried in 2^-48 fixed point;
+//   - band cells are queued per warp and evaluated 32 at a time, so the FP64
+//     inversion of the profile runs with every lane busy.
 template <class S> struct Scr { using T = float; };
 template <> struct Scr<double> { using T = double; };
 template <class S> __device__ __forceinline__ typename Scr<S>::T scr(const S *f, long long i);
@@ -128,43 +139,256 @@ template <> __device__ __forceinline__ float scr<__nv_bfloat16>(const __nv_bfloa
     return __bfloat162float(f[i]);
 }
 
-// Partial sums of one block over its contiguous range of rows: block b of nb
-// takes rows [b * rows / nb, (b + 1) * rows / nb), rows ordered (j fastest, k).
+// 16 bytes of a row as storage elements, widened to the screening type
+template <class S> struct Row16;
+template <> struct Row16<float> {
+    static constexpr int E = 4;
+    static __device__ __forceinline__ float get(const uint4 &w, int e)
+    {
+        return __uint_as_float(e == 0 ? w.x : e == 1 ? w.y : e == 2 ? w.z : w.w);
+    }
+};
+template <> struct Row16<__nv_bfloat16> {
+    static constexpr int E = 8;
+    static __device__ __forceinline__ float get(const uint4 &w, int e)
+    {
+        const unsigned u = (e >> 1) == 0 ? w.x : (e >> 1) == 1 ? w.y : (e >> 1) == 2 ? w.z : w.w;
+        return __uint_as_float((e & 1) ? (u & 0xffff0000u) : (u << 16));
+    }
+};
+template <> struct Row16<double> {
+    static constexpr int E = 2;
+    static __device__ __forceinline__ double get(const uint4 &w, int e)
+    {
+        return e == 0 ? __hiloint2double((int)w.y, (int)w.x) : __hiloint2double((int)w.w, (int)w.z);
+    }
+};
+
+__device__ __forceinline__ bool in_band(float x)
+{
+    return x >= __double2float_ru(1e-6) && x <= __double2float_rd(1.0 - 1e-6);
+}
+__device__ __forceinline__ bool in_band(double x) { return x > 1e-6 && x < 1.0 - 1e-6; }
+
+// y * 2^48 truncated toward zero, for |y| < 2^14 (the bits below 2^-48 drop)
+__device__ __forceinline__ long long fix48(float y)
+{
+    const unsigned b = __float_as_uint(y);
+    const int E = (int)((b >> 23) & 0xffu);
+    if (E < 78) return 0;   // |y| < 2^-49
+    const long long m = (long long)((b & 0x7fffffu) | 0x800000u);   // |y| = m 2^(E - 150)
+    const int sh = E - 102;
+    const long long v = sh >= 0 ? (m << sh) : (m >> (-sh));
+    return (b >> 31) ? -v : v;
+}
+
+// Volume of one lane.  FP32 values: each row as an unevaluated pair s + c
+// (TwoSum), then the pair in 2^-48 fixed point (exact to the dropped bits,
+// below 4e-15 per row), carried into FP64 every 64 rows, before the fixed
+// point could overflow.
+template <class R> struct VolSum;
+template <> struct VolSum<float> {
+    float s = 0.0f, c = 0.0f;
+    long long fix = 0;
+    double sum = 0.0;
+    int rows = 0;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float t = s + x, z = t - s;
+        c += (s - (t - z)) + (x - z);
+        s = t;
+    }
+    __device__ __forceinline__ void end_row()
+    {
+        if (fabsf(s) < 256.0f) fix += fix48(s) + fix48(c);
+        else sum += (double)s + (double)c;
+        s = c = 0.0f;
+        if (++rows == 64) {
+            sum += (double)fix * 0x1p-48;
+            fix = 0;
+            rows = 0;
+        }
+    }
+    __device__ __forceinline__ double total() const { return sum + (double)fix * 0x1p-48; }
+};
+template <> struct VolSum<double> {
+    double sum = 0.0;
+    __device__ __forceinline__ void add(double x) { sum += x; }
+    __device__ __forceinline__ void end_row() {}
+    __device__ __forceinline__ double total() const { return sum; }
+};
+
+// (ln F_j, 1 / F_j) for F_j = 1 + j/256
+__device__ double2 g_ln_table[256];
+
+__global__ void ln_table_kernel()
+{
+    const double F = 1.0 + threadIdx.x / 256.0;
+    g_ln_table[threadIdx.x] = make_double2(log(F), 1.0 / F);
+}
+
+// ln y for a normal y in (0, 1], table-driven (Tang, ACM TOMS 16, 1990):
+// y = 2^k m, m in [1, 2); F = 1 + j/256 takes the top 8 fraction bits of m, so
+// f = m - F is exact and u = f/F lies in [0, 2^-8).  ln(1 + u) is its Taylor
+// series: u - u^2/2 in FP64, the terms u^3/3 - u^4/4 + u^5/5 (below 2e-8) in
+// FP32, truncation below u^6/6 < 6e-16.  Returned as k, ln F and ln(1 + u).
+struct LnParts {
+    int k;
+    double lnF, s;
+};
+__device__ __forceinline__ LnParts ln_parts(double y, const double2 *tab)
+{
+    const int hi = __double2hiint(y), lo = __double2loint(y);
+    const int j = (hi >> 12) & 0xff;
+    const double m = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, lo);
+    const double F = __hiloint2double(0x3ff00000 | (j << 12), 0);
+    const double2 t = tab[j];
+    const double u = (m - F) * t.y;
+    const float uf = (float)u;
+    const float tail = uf * uf * uf * fmaf(uf, fmaf(uf, 0.2f, -0.25f), 1.0f / 3.0f);
+    LnParts r;
+    r.k = ((hi >> 20) & 0x7ff) - 1023;
+    r.lnF = t.x;
+    r.s = fma(-0.5 * u, u, u) + (double)tail;
+    return r;
+}
+
+// one band cell waiting in its warp's queue: value, x index, and its row's
+// share of p.n and of |p - ctr|^2
+template <class R> struct BandCell {
+    R phi;
+    int i;
+    double pn_row, ryz2;
+};
+
+// Sec. 2.3 sums of one band cell: q = phi(1 - phi), psi = (lambda/2) artanh(1 - 2 phi)
+// = (lambda/4) (ln(1 - phi) - ln phi), p = dx (i, j, k)
+struct BandConst {
+    double dxn0, dx, c0, quarter_lambda;
+};
+template <class R>
+__device__ __forceinline__ void band_cell(const BandConst &bc, const BandCell<R> &c, const double2 *tab, double *v)
+{
+    const double ph = (double)c.phi;
+    const double om = 1.0 - ph;   // exact
+    const double q = ph * om;
+    const LnParts l1 = ln_parts(om, tab), l0 = ln_parts(ph, tab);
+    const double d = fma((double)(l1.k - l0.k), 0.69314718055994530942, (l1.lnF - l0.lnF) + (l1.s - l0.s));
+    const double psi = bc.quarter_lambda * d;
+    const double di = (double)c.i;
+    const double pn = fma(di, bc.dxn0, c.pn_row);
+    const double rx = fma(di, bc.dx, -bc.c0);
+    const double r = sqrt(fma(rx, rx, c.ryz2));
+    v[1] += q;
+    v[2] += q * (pn - psi);
+    v[3] += q * (r + psi);
+}
+
+// Partial sums of block b of nb (256 threads): rows ordered (j fastest, k) are
+// dealt round-robin to the nb * 8 warps, so every block samples the whole
+// grid and the band work (which sits in a few planes) is spread evenly.
 template <class S>
 __device__ __forceinline__ void stats_pass(const StatsArgs &a, const S *f, double *partial_out,
                                            long long blk, long long nblk)
 {
     using R = typename Scr<S>::T;
+    constexpr int E = Row16<S>::E;        // elements per 16-byte load
+    constexpr int V = 16 / E;             // loads per lane and sweep
+    constexpr int kWarps = 8;
+    __shared__ BandCell<R> queue[kWarps][64];
+    const double2 *tab = g_ln_table;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    BandCell<R> *qw = queue[warp];
     double v[kNStat];
 #pragma unroll
     for (int i = 0; i < kNStat; ++i) v[i] = 0.0;
     R mn = R(INFINITY), mx = R(-INFINITY);
-    const double e_pref = a.Gamma / (a.C_gamma * a.lambda);
-    const int nd = a.stencil == 6 ? 3 : (a.stencil == 18 ? 9 : 13);
-    const R lo = R(0.5e-6), hi = R(1.0 - 0.5e-6);   // conservative pre-filter of the FP64 band test
+    int nonfinite = 0, cnt = 0;
+    const BandConst bconst = {a.dx * a.n[0], a.dx, a.ctr[0], 0.25 * a.lambda};
+    VolSum<R> vol;
     const long long rows = (long long)a.g.ny * a.g.nz;
-    const long long r0 = blk * rows / nblk, r1 = (blk + 1) * rows / nblk;
-    int j = (int)(r0 % a.g.ny), k = (int)(r0 / a.g.ny);
-    for (long long row = r0; row < r1; ++row) {
-        const long long rbase = cell_index(a.g, 0, j, k);
-        for (int i = threadIdx.x; i < a.g.nx; i += blockDim.x) {
-            const R r = scr<S>(f, rbase + i);
-            if (!isfinite(r)) { v[6] += 1.0; continue; }
-            const double ph = (double)r;   // exact
-            v[0] += ph;
-            mn = r < mn ? r : mn;
-            mx = r > mx ? r : mx;
-            if (r > lo && r < hi && ph > 1e-6 && ph < 1.0 - 1e-6) {
-                const double q = ph * (1.0 - ph);
-                const double psi = 0.5 * a.lambda * atanh(1.0 - 2.0 * ph);
-                const double px = a.dx * i, py = a.dx * j, pz = a.dx * k;
-                const double pn = px * a.n[0] + py * a.n[1] + pz * a.n[2];
-                const double rx = px - a.ctr[0], ry = py - a.ctr[1], rz = pz - a.ctr[2];
-                v[1] += q;
-                v[2] += q * (pn - psi);
-                v[3] += q * (sqrt(rx * rx + ry * ry + rz * rz) + psi);
+    const int nvec = (a.g.nx + E - 1) / E;
+    for (long long row = blk * kWarps + warp; row < rows; row += nblk * kWarps) {
+        const int j = (int)(row % a.g.ny), k = (int)(row / a.g.ny);
+        double pn_row = 0.0, ryz2 = 0.0;   // the row's shares, once it has band cells
+        bool row_known = false;
+        const uint4 *src = (const uint4 *)(f + cell_index(a.g, 0, j, k));
+        for (int v0 = 0; v0 < nvec; v0 += 32 * V) {
+            uint4 w[V];
+#pragma unroll
+            for (int t = 0; t < V; ++t) {
+                const int vi = v0 + 32 * t + lane;
+                w[t] = vi < nvec ? __ldg(src + vi) : make_uint4(0u, 0u, 0u, 0u);
             }
-            if (a.energy) {
+            unsigned bm = 0u;   // band cells of this lane among its E * V
+#pragma unroll
+            for (int t = 0; t < V; ++t)
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int i = (v0 + 32 * t + lane) * E + e;
+                    const R x = Row16<S>::get(w[t], e);
+                    if (i < a.g.nx) {
+                        if (!isfinite(x)) {
+                            ++nonfinite;
+                        } else {
+                            vol.add(x);
+                            mn = x < mn ? x : mn;
+                            mx = x > mx ? x : mx;
+                            if (in_band(x)) bm |= 1u << (t * E + e);
+                        }
+                    }
+                }
+            // queue this sweep's band cells, evaluating full warps of them
+            if (!row_known && __any_sync(0xffffffffu, bm != 0u)) {
+                const double py = a.dx * j, pz = a.dx * k;
+                pn_row = py * a.n[1] + pz * a.n[2];
+                const double ry = py - a.ctr[1], rz = pz - a.ctr[2];
+                ryz2 = ry * ry + rz * rz;
+                row_known = true;
+            }
+            while (__any_sync(0xffffffffu, bm != 0u)) {
+                const int b = bm ? __ffs(bm) - 1 : -1;
+                bm &= bm - 1u;
+                R x = R(0);
+#pragma unroll
+                for (int u = 0; u < E * V; ++u) x = b == u ? Row16<S>::get(w[u / E], u % E) : x;
+                const unsigned m = __ballot_sync(0xffffffffu, b >= 0);
+                if (b >= 0) {
+                    BandCell<R> &c = qw[cnt + __popc(m & ((1u << lane) - 1u))];
+                    c.phi = x;
+                    c.i = (v0 + 32 * (b / E) + lane) * E + b % E;
+                    c.pn_row = pn_row;
+                    c.ryz2 = ryz2;
+                }
+                cnt += __popc(m);
+                if (cnt >= 32) {
+                    __syncwarp();
+                    band_cell<R>(bconst, qw[lane], tab, v);
+                    __syncwarp();
+                    cnt -= 32;
+                    if (lane < cnt) qw[lane] = qw[lane + 32];
+                    __syncwarp();
+                }
+            }
+        }
+        vol.end_row();
+    }
+    v[0] = vol.total();
+    __syncwarp();
+    if (lane < cnt) band_cell<R>(bconst, qw[lane], tab, v);
+    v[4] = (double)mn;
+    v[5] = (double)mx;
+    v[6] = (double)nonfinite;
+    if (a.energy) {   // Eq. 1 at dF = 0, one cell per thread, contiguous rows per block
+        const long long r0 = blk * rows / nblk, r1 = (blk + 1) * rows / nblk;
+        const double e_pref = a.Gamma / (a.C_gamma * a.lambda);
+        const int nd = a.stencil == 6 ? 3 : (a.stencil == 18 ? 9 : 13);
+        for (long long row = r0; row < r1; ++row) {
+            const int j = (int)(row % a.g.ny), k = (int)(row / a.g.ny);
+            const long long rbase = cell_index(a.g, 0, j, k);
+            for (int i = threadIdx.x; i < a.g.nx; i += blockDim.x) {
+                const double ph = rd<S>(f, rbase + i);
+                if (!isfinite(ph)) continue;
                 double e = 0.0;
                 for (int kk = 0; kk < nd; ++kk) {
                     const Dir d = grid_dir(kk);
@@ -177,10 +401,7 @@ __device__ __forceinline__ void stats_pass(const StatsArgs &a, const S *f, doubl
                 v[7] += e_pref * e;
             }
         }
-        if (++j == a.g.ny) { j = 0; ++k; }
     }
-    v[4] = (double)mn;
-    v[5] = (double)mx;
     block_reduce_store(v, partial_out);
 }
 
@@ -232,18 +453,68 @@ size_t grid_scratch_bytes()
     return scratch_err_offset() + 16;
 }
 
+// The logarithm table of the band evaluation, written once per device by a
+// kernel on the calling stream and waited for, so that calls on other streams
+// can rely on it.  Inside a stream capture the writer is recorded into the
+// graph instead (it cannot be waited for there) and the device stays unmarked.
+static cudaError_t ensure_ln_table(cudaStream_t st)
+{
+    static std::mutex mu;
+    static bool ready[128];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (ready[dev]) return cudaSuccess;
+    ln_table_kernel<<<1, 256, 0, st>>>();
+    e = cudaGetLastError();
+    if (e != cudaSuccess || cs != cudaStreamCaptureStatusNone) return e;
+    e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) ready[dev] = true;
+    return e;
+}
+
+// One full wave of stats blocks on this device (at most kStatsBlocks): the
+// pass is bound by the FP64 pipe, so a partial second wave would idle SMs.
+template <class S> static int stats_blocks()
+{
+    static int cached[128];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return kStatsBlocks;
+    if (!cached[dev]) {
+        int per = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, stats_kernel<S>, 256, 0) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return kStatsBlocks;
+        const int n = per * sms;
+        cached[dev] = n < 1 ? 1 : (n > kStatsBlocks ? kStatsBlocks : n);
+    }
+    return cached[dev];
+}
+
 cudaError_t launch_stats(const StatsArgs &a, const void *field, double *partials, double *final_out,
                          cudaStream_t st)
 {
-    if (a.dtype == SPFM_F64)
-        stats_kernel<double><<<kStatsBlocks, 256, 0, st>>>(a, (const double *)field, partials);
-    else if (a.dtype == SPFM_F32)
-        stats_kernel<float><<<kStatsBlocks, 256, 0, st>>>(a, (const float *)field, partials);
-    else
-        stats_kernel<__nv_bfloat16><<<kStatsBlocks, 256, 0, st>>>(a, (const __nv_bfloat16 *)field, partials);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = ensure_ln_table(st);
     if (e != cudaSuccess) return e;
-    stats_final_kernel<<<1, 256, 0, st>>>(partials, kStatsBlocks, final_out);
+    int nb;
+    if (a.dtype == SPFM_F64) {
+        nb = stats_blocks<double>();
+        stats_kernel<double><<<nb, 256, 0, st>>>(a, (const double *)field, partials);
+    } else if (a.dtype == SPFM_F32) {
+        nb = stats_blocks<float>();
+        stats_kernel<float><<<nb, 256, 0, st>>>(a, (const float *)field, partials);
+    } else {
+        nb = stats_blocks<__nv_bfloat16>();
+        stats_kernel<__nv_bfloat16><<<nb, 256, 0, st>>>(a, (const __nv_bfloat16 *)field, partials);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    stats_final_kernel<<<1, 256, 0, st>>>(partials, nb, final_out);
     return cudaGetLastError();
 }
 
@@ -251,11 +522,13 @@ cudaError_t launch_stats_batch(const StatsJob *jobs, int n, int dtype, double *p
                                cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
+    cudaError_t e = ensure_ln_table(st);
+    if (e != cudaSuccess) return e;
     const dim3 grid(kBatchStatsBlocks, n);
     if (dtype == SPFM_F64) stats_batch_kernel<double><<<grid, 256, 0, st>>>(jobs, partials);
     else if (dtype == SPFM_F32) stats_batch_kernel<float><<<grid, 256, 0, st>>>(jobs, partials);
     else stats_batch_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(jobs, partials);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     stats_final_kernel<<<n, 256, 0, st>>>(partials, kBatchStatsBlocks, finals);
     return cudaGetLastError();

@@ -145,6 +145,43 @@ def test_stats_and_energy_match_oracle(dtype):
     assert abs(st["radius"] - ref["radius"]) <= (1e-12 if dtype == S.SPFM_F64 else 1e-6)
 
 
+@pytest.mark.parametrize("dtype", [S.SPFM_F64, S.SPFM_F32, S.SPFM_BF16])
+def test_stats_value_mix_matches_oracle(dtype):
+    """Every kind of value the stats pass screens differently: exact 0 and 1,
+    band values, values a few ulps either side of both band limits, tiny
+    (down to subnormal) and negative values, and a few large ones (rows whose
+    sum leaves the fixed-point range), on a ragged x extent, with many
+    32-cell flushes of the band queue and a partial one at the end."""
+    nx, ny, nz = 203, 17, 11
+    n = rng_normal(11)
+    ctr = (101.3, 8.2, 5.7)
+    g = S.Grid(nx, ny, nz, dtype=dtype, n=n, center=ctr)
+    p = O.Params(nx, ny, nz, n=tuple(n), lam=3.0)
+    rng = np.random.default_rng(12)
+    shape = p.shape
+    kind = rng.integers(0, 9, size=shape)
+    u = rng.uniform(-1.0, 1.0, size=shape)
+    choices = [
+        np.zeros(shape), np.ones(shape), rng.uniform(0.0, 1.0, size=shape),
+        1e-6 * (1.0 + 1e-6 * u),                   # around the lower band limit
+        (1.0 - 1e-6) + 3e-7 * u,                   # around the upper band limit
+        10.0 ** rng.uniform(-42.0, -7.0, size=shape),
+        -rng.uniform(0.0, 1e-3, size=shape),
+        1.0 + rng.uniform(0.0, 1e-5, size=shape),
+        rng.uniform(0.0, 1.0, size=shape),
+    ]
+    phi = np.choose(kind, choices)
+    phi[3, 5, 7] = 300.0
+    phi[9, 16, 200] = 5e3
+    start = upload(g, phi, dtype)
+    g.step(0, lam=3.0, dt=0.05)
+    st = g.stats()
+    ref = O.stats(p, start, ctr)
+    assert ref["S_w"] > 0.0
+    for k in ("volume", "S_w", "S_c", "S_r", "phi_min", "phi_max", "position", "radius"):
+        assert abs(st[k] - ref[k]) <= 1e-12 * max(1.0, abs(ref[k])), (k, st[k], ref[k])
+
+
 # --------------------------------------------------------------- config 1
 
 
