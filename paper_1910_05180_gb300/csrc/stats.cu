@@ -253,6 +253,16 @@ __device__ __forceinline__ LnParts ln_parts(double y, const double2 *tab)
     return r;
 }
 
+// sqrt(r2) in FP64 from the FP32 square root and one Newton step in FP64
+// (relative error below 2e-14); 0, tiny, huge and non-finite r2 take sqrt
+__device__ __forceinline__ double dist_from_r2(double r2)
+{
+    const float rf = sqrtf((float)r2);
+    if (!(rf > 1e-15f && rf < 1e15f)) return sqrt(r2);
+    const double r0 = (double)rf;
+    return fma(fma(-r0, r0, r2), (double)(0.5f / rf), r0);
+}
+
 // one band cell waiting in its warp's queue: value, x index, and its row's
 // share of p.n and of |p - ctr|^2
 template <class R> struct BandCell {
@@ -278,7 +288,7 @@ __device__ __forceinline__ void band_cell(const BandConst &bc, const BandCell<R>
     const double di = (double)c.i;
     const double pn = fma(di, bc.dxn0, c.pn_row);
     const double rx = fma(di, bc.dx, -bc.c0);
-    const double r = sqrt(fma(rx, rx, c.ryz2));
+    const double r = dist_from_r2(fma(rx, rx, c.ryz2));
     v[1] += q;
     v[2] += q * (pn - psi);
     v[3] += q * (r + psi);

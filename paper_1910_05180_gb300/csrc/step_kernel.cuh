@@ -4,16 +4,21 @@
 // (spfm_internal.h), so a tile plus its halo is a set of plain, in-bounds,
 // 16-byte-aligned rows.  One CTA owns an xy tile of TX*VX by TY cells
 // (VX = cells per 16 bytes) and marches a chunk of z planes.  A producer warp
-// copies each plane's TY+2 halo rows into a ring of NS shared-memory stages
-// with bulk asynchronous copies (cp.async.bulk, completed on an mbarrier with
-// a transaction count); TX*TY consumer threads wait on the stage's "full"
-// barrier, read it, and release it on its "empty" barrier.  There is no
-// __syncthreads in the march, and NS-1 planes stay in flight per CTA.  Every
-// wait is bounded: on timeout the thread sets the error word and leaves.
+// brings each plane's tile plus halo into a ring of NS shared-memory stages
+// with one TMA tensor copy (cp.async.bulk.tensor.3d over a tensor map of the
+// ghosted buffer), or, where no map could be encoded, with one bulk copy per
+// halo row (cp.async.bulk); both complete on the stage's "full" mbarrier by
+// transaction count.  TX*TY consumer threads wait on "full", read the stage,
+// and release it on its "empty" barrier.  There is no __syncthreads in the
+// march, and NS-1 planes stay in flight per CTA.  Every wait is bounded: on
+// timeout the thread sets the error word and leaves.
 //
 // Boundary conditions.  The kernel reads the ghost layer and writes interior
 // cells only; a face kernel (boundary.cu) refreshes the ghosts of the new
-// field after each step, so the hot path holds no boundary logic.
+// field after each step, so the hot path holds no boundary logic.  Under
+// programmatic dependent launch the next step starts while that kernel runs:
+// tiles whose halo touches a face wait for it (griddepcontrol.wait), interior
+// tiles do not.
 //
 // Arithmetic.  From each plane every thread forms, for its cells,
 //   C  = phi at the cell,
