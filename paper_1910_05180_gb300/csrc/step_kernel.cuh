@@ -69,6 +69,7 @@ template <> struct Pk<float> {
         asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(b.y));
         return __fmul2_rn(a, r);
     }
+    static __device__ __forceinline__ P rsqrt(P a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
 };
 
 struct D2 { double x, y; };
@@ -82,8 +83,9 @@ template <> struct Pk<double> {
     {
         return {__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y)};
     }
-    static __device__ __forceinline__ P sub(P a, P b) { return {a.x - b.x, a.y - b.y}; }
+    static __device__ __forceinline__ P sub(P a, P b) { return {__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y)}; }
     static __device__ __forceinline__ P div(P a, P b) { return {a.x / b.x, a.y / b.y}; }
+    static __device__ __forceinline__ P rsqrt(P a) { return {::rsqrt(a.x), ::rsqrt(a.y)}; }
 };
 
 template <class T> struct PackT;
@@ -317,51 +319,99 @@ __device__ __forceinline__ typename Pk<T>::P psi_pack(typename Pk<T>::P v, T qua
 {
     return Pk<T>::mk(psi_of(v.x, quarter_lam, eps), psi_of(v.y, quarter_lam, eps));
 }
-__device__ __forceinline__ float tanh_of(float x) { return tanhf(x); }
-__device__ __forceinline__ double tanh_of(double x) { return tanh(x); }
+// tanh of a pack.  FP32: Lambert's continued fraction for tanh truncated
+// after the term x^2/11, x (10395 + 1260 y + 21 y^2) / (10395 + 4725 y + 210 y^2 + y^3)
+// with y = x^2 (|error| < 3.3e-10 for |x| <= 1, < 3e-8 for |x| <= 1.5); callers
+// whose arguments can exceed 1.5 pass small = false and get tanhf.  FP64: tanh.
+template <class T> struct TanhPk;
+template <> struct TanhPk<float> {
+    static __device__ __forceinline__ float2 eval(float2 x, bool small)
+    {
+        if (!small) return make_float2(tanhf(x.x), tanhf(x.y));
+        const float2 y = __fmul2_rn(x, x);
+        const float2 num = __ffma2_rn(__ffma2_rn(y, make_float2(21.f, 21.f), make_float2(1260.f, 1260.f)), y,
+                                      make_float2(10395.f, 10395.f));
+        const float2 den = __ffma2_rn(__ffma2_rn(__fadd2_rn(y, make_float2(210.f, 210.f)), y,
+                                                 make_float2(4725.f, 4725.f)),
+                                      y, make_float2(10395.f, 10395.f));
+        return Pk<float>::div(__fmul2_rn(x, num), den);
+    }
+};
+template <> struct TanhPk<double> {
+    static __device__ __forceinline__ D2 eval(D2 x, bool) { return {tanh(x.x), tanh(x.y)}; }
+};
 
-// TI_n factor w = -dt (potential / q + 4 M dF / (lambda Gamma)) of one cell with
-// phi, s = 1 - 2 phi, u = s^2 and the profile-inversion gradient g (Sec. 2.1,
-// TI_n): n = g / |g|, t_i = tanh(2 dx n_i / lambda), the 13 couplings from the
-// tanh addition theorem (a = N / D), and the potential sum
+// TI_n factor w = -dt (potential / q + 4 M dF / (lambda Gamma)) of a pack of
+// cells with s = 1 - 2 phi, u = s^2 and the profile-inversion gradient g
+// (Sec. 2.1, TI_n): n = g / |g|, t_i = tanh(2 dx n_i / lambda), the 13
+// couplings a = N / D from the tanh addition theorem, and the potential sum
 // sum_k 4 c_k a_k^2 / (1 - a_k^2 s^2) = sum_k 4 c_k N^2 / (D^2 - N^2 s^2).
-// Where |g| < 1e-8 the normal is undefined and the cell takes the CF potential.
-template <class T>
-__device__ __forceinline__ T ti_local_w(const StepCoef<T> &C, T s, T u, T gx, T gy, T gz)
+// c_k is one value per shell, so each shell's terms are summed as one running
+// fraction and the three shells are joined with one reciprocal.  Where
+// |g| < 1e-8 the normal is undefined and the cell takes the CF potential.
+template <class T, int STENCIL>
+__device__ __forceinline__ typename Pk<T>::P ti_local_w(const StepCoef<T> &C, typename Pk<T>::P sg,
+                                                        typename Pk<T>::P u, typename Pk<T>::P gx,
+                                                        typename Pk<T>::P gy, typename Pk<T>::P gz)
 {
-    const T g2 = gx * gx + gy * gy + gz * gz;
-    if (!(g2 >= T(1e-16))) return s * (-C.dt * C.kappa) - C.dt * C.kmu;
-    const T inv = T(1) / sqrt(g2);
-    const T k2 = C.two_dx_over_lam;
-    const T tx = tanh_of(k2 * gx * inv), ty = tanh_of(k2 * gy * inv), tz = tanh_of(k2 * gz * inv);
-    T sum = T(0);
-    auto term = [&](T ck, T N, T D) {
-        const T N2 = N * N;
-        sum += T(4) * ck * N2 / (D * D - N2 * u);
+    using K = Pk<T>;
+    using P = typename K::P;
+    const P one = K::mk(T(1), T(1));
+    const P zero = K::mk(T(0), T(0));
+    const P neg_u = K::sub(zero, u);   // -s^2
+    const P g2 = K::fma(gx, gx, K::fma(gy, gy, K::mul(gz, gz)));
+    const P kin = K::mul(K::mk(C.two_dx_over_lam, C.two_dx_over_lam), K::rsqrt(g2));
+    const bool small = C.two_dx_over_lam <= T(1.5);
+    const P a = TanhPk<T>::eval(K::mul(gx, kin), small);
+    const P b = TanhPk<T>::eval(K::mul(gy, kin), small);
+    const P c = TanhPk<T>::eval(K::mul(gz, kin), small);
+    // (num, den) += n / d as one fraction
+    auto acc = [&](P &num, P &den, P n, P d) {
+        num = K::fma(num, d, K::mul(n, den));
+        den = K::mul(den, d);
     };
-    // shell 1: (1,0,0), (0,1,0), (0,0,1)
-    term(C.ck[0], tx, T(1));
-    term(C.ck[1], ty, T(1));
-    term(C.ck[2], tz, T(1));
-    if (C.ck[3] != T(0)) {
+    // shell 1: N = t_i, D = 1
+    const P a2 = K::mul(a, a), b2 = K::mul(b, b), c2 = K::mul(c, c);
+    P n1 = a2, d1 = K::fma(a2, neg_u, one);
+    acc(n1, d1, b2, K::fma(b2, neg_u, one));
+    acc(n1, d1, c2, K::fma(c2, neg_u, one));
+    P num = K::mul(K::mk(T(-4) * C.dt * C.ck[0], T(-4) * C.dt * C.ck[0]), n1), den = d1;
+    if (STENCIL >= 18 && C.ck[3] != T(0)) {
         // shell 2: (1,1,0), (0,1,1), (1,0,1), (1,-1,0), (0,1,-1), (1,0,-1)
-        term(C.ck[3], tx + ty, T(1) + tx * ty);
-        term(C.ck[4], ty + tz, T(1) + ty * tz);
-        term(C.ck[5], tx + tz, T(1) + tx * tz);
-        term(C.ck[6], tx - ty, T(1) - tx * ty);
-        term(C.ck[7], ty - tz, T(1) - ty * tz);
-        term(C.ck[8], tx - tz, T(1) - tx * tz);
+        P n2 = zero, d2 = one;
+        auto pair = [&](P x, P y) {
+            const P xy = K::mul(x, y);
+            const P np = K::add(x, y), dp = K::add(one, xy);
+            const P nm = K::sub(x, y), dm = K::sub(one, xy);
+            const P np2 = K::mul(np, np), nm2 = K::mul(nm, nm);
+            acc(n2, d2, np2, K::fma(np2, neg_u, K::mul(dp, dp)));
+            acc(n2, d2, nm2, K::fma(nm2, neg_u, K::mul(dm, dm)));
+        };
+        pair(a, b);
+        pair(b, c);
+        pair(a, c);
+        acc(num, den, K::mul(K::mk(T(-4) * C.dt * C.ck[3], T(-4) * C.dt * C.ck[3]), n2), d2);
     }
-    if (C.ck[9] != T(0)) {
+    if (STENCIL >= 26 && C.ck[9] != T(0)) {
         // shell 3: (1,1,1), (-1,1,1), (1,-1,1), (1,1,-1):
-        // tanh(a + b + c) = (ta + tb + tc + ta tb tc) / (1 + ta tb + tb tc + ta tc)
-        auto t3 = [&](T a, T b, T c) { term(C.ck[9], a + b + c + a * b * c, T(1) + a * b + b * c + a * c); };
-        t3(tx, ty, tz);
-        t3(-tx, ty, tz);
-        t3(tx, -ty, tz);
-        t3(tx, ty, -tz);
+        // tanh(x + y + z) = (tx + ty + tz + tx ty tz) / (1 + tx ty + ty tz + tx tz)
+        const P ab = K::mul(a, b), bc = K::mul(b, c), ca = K::mul(c, a), abc = K::mul(ab, c);
+        P n3 = zero, d3 = one;
+        auto term = [&](P N, P D) {
+            const P N2 = K::mul(N, N);
+            acc(n3, d3, N2, K::fma(N2, neg_u, K::mul(D, D)));
+        };
+        term(K::add(K::add(a, b), K::add(c, abc)), K::add(K::add(one, ab), K::add(bc, ca)));
+        term(K::sub(K::add(b, c), K::add(a, abc)), K::sub(K::add(one, bc), K::add(ab, ca)));
+        term(K::sub(K::add(a, c), K::add(b, abc)), K::sub(K::add(one, ca), K::add(ab, bc)));
+        term(K::sub(K::add(a, b), K::add(c, abc)), K::sub(K::add(one, ab), K::add(bc, ca)));
+        acc(num, den, K::mul(K::mk(T(-4) * C.dt * C.ck[9], T(-4) * C.dt * C.ck[9]), n3), d3);
     }
-    return s * (-C.dt * sum) - C.dt * C.kmu;
+    const P nkmu = K::mk(-C.dt * C.kmu, -C.dt * C.kmu);
+    const P w = K::fma(sg, K::div(num, den), nkmu);
+    const P wcf = K::fma(sg, K::mk(-C.dt * C.kappa, -C.dt * C.kappa), nkmu);
+    const T lim = T(1e-16);
+    return K::mk(g2.x >= lim ? w.x : wcf.x, g2.y >= lim ? w.y : wcf.y);
 }
 
 // The packs of one staged row around a thread's cells (adjacent pairs):
@@ -496,13 +546,48 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
                     }
                 }
                 if (KIND == 6) {
-                    // psi at the cells and central differences along x and y
+                    // psi at the cells and central differences along x and y.  A
+                    // warp holds 32/TX rows: each lane inverts its own cells and
+                    // its row's two x-neighbour cells; the rows above and below
+                    // come by shuffle from the lanes TX away, except beyond the
+                    // warp's first and last rows, where the lane inverts them.
+                    static_assert(KIND != 6 || (TX <= 16 && 32 % TX == 0), "TI_n needs two or more rows a warp");
                     const T ql = C.half_lam * T(0.5), ep = C.eps;
+                    const bool first = lane < TX, last = lane >= 32 - TX;
+                    T own[VX], outer[VX];
 #pragma unroll
                     for (int q = 0; q < NP; ++q) {
-                        p[r].psi[q] = psi_pack<T>(rc[r + 1][q], ql, ep);
-                        p[r].gx[q] = K::sub(psi_pack<T>(re[r + 1][q], ql, ep), psi_pack<T>(rw[r + 1][q], ql, ep));
-                        p[r].gy[q] = K::sub(psi_pack<T>(rc[r + 2][q], ql, ep), psi_pack<T>(rc[r][q], ql, ep));
+                        const P po = psi_pack<T>(rc[r + 1][q], ql, ep);
+                        const P pb = psi_pack<T>(first ? rc[r][q] : rc[r + 2][q], ql, ep);
+                        p[r].psi[q] = po;
+                        own[2 * q] = po.x;
+                        own[2 * q + 1] = po.y;
+                        outer[2 * q] = pb.x;
+                        outer[2 * q + 1] = pb.y;
+                    }
+                    // the two x-neighbour cells of the thread's run
+                    const P pwe = psi_pack<T>(K::mk(rw[r + 1][0].x, re[r + 1][NP - 1].y), ql, ep);
+                    const T pw = pwe.x;   // x - 1
+                    const T pe = pwe.y;   // x + VX
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) {
+                        const T w0 = 2 * q == 0 ? pw : own[2 * q - 1];
+                        const T e1 = 2 * q + 2 == VX ? pe : own[2 * q + 2];
+                        // K::sub is an explicit fused op that the compiler cannot merge
+                        // with the multiply inside psi: equal psi then differ by exactly
+                        // zero, and a clamped region keeps the CF fallback (a contracted
+                        // difference leaves the rounding error of that multiply, enough
+                        // to pass |g| >= 1e-8 in FP32 with a meaningless normal)
+                        p[r].gx[q] = K::sub(K::mk(own[2 * q + 1], e1), K::mk(w0, own[2 * q]));
+                        T nb[2], sb[2];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const T up = __shfl_up_sync(0xffffffffu, own[2 * q + h], TX);
+                            const T dn = __shfl_down_sync(0xffffffffu, own[2 * q + h], TX);
+                            nb[h] = first ? outer[2 * q + h] : up;   // row j - 1
+                            sb[h] = last ? outer[2 * q + h] : dn;    // row j + 1
+                        }
+                        p[r].gy[q] = K::sub(K::mk(sb[0], sb[1]), K::mk(nb[0], nb[1]));   // psi(j + 1) - psi(j - 1)
                     }
                 }
             }
@@ -526,10 +611,9 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
                         w = K::fma(sg, PC.nkap, PC.nkmu);
                     } else if (KIND == 6) {
                         const P u = K::mul(sg, sg);
-                        const P gz = K::sub(p[r].psi[q], m[r].psi[q]);
-                        const T s2 = C.inv_2dx;
-                        w = K::mk(ti_local_w<T>(C, sg.x, u.x, z[r].gx[q].x * s2, z[r].gy[q].x * s2, gz.x * s2),
-                                  ti_local_w<T>(C, sg.y, u.y, z[r].gx[q].y * s2, z[r].gy[q].y * s2, gz.y * s2));
+                        const P s2 = K::mk(C.inv_2dx, C.inv_2dx);
+                        const P gz = K::mul(K::sub(p[r].psi[q], m[r].psi[q]), s2);
+                        w = ti_local_w<T, STENCIL>(C, sg, u, K::mul(z[r].gx[q], s2), K::mul(z[r].gy[q], s2), gz);
                     } else {
                         const P u = K::mul(sg, sg);
                         P num = PC.nbeta[0];
