@@ -376,36 +376,40 @@ __device__ __forceinline__ typename Pk<T>::P ti_local_w(const StepCoef<T> &C, ty
     acc(n1, d1, b2, K::fma(b2, neg_u, one));
     acc(n1, d1, c2, K::fma(c2, neg_u, one));
     P num = K::mul(K::mk(T(-4) * C.dt * C.ck[0], T(-4) * C.dt * C.ck[0]), n1), den = d1;
+    // Shells 2 and 3 come in pairs of directions whose couplings are
+    // N = x +- y, D = y' +- x' for one (x, y, x', y').  With S = x^2 + y^2,
+    // B = x'^2 + y'^2 (S and B are the squares summed over the pair), R = 2 x y
+    // (= 2 x' y'), P = B - S u and v = 1 - u, the pair's two terms
+    // n/d = (S +- R) / (P +- R v) add up to 2 (S P - R^2 v) / (P^2 - R^2 v^2).
+    const P v = K::add(one, neg_u);
+    const P m4 = K::mk(T(-4), T(-4));
+    auto pair = [&](P &pn, P &pd, P S, P B, P r) {   // r = x^2 y^2 = R^2 / 4
+        const P Pv = K::fma(S, neg_u, B);
+        const P rv = K::mul(r, v);
+        acc(pn, pd, K::fma(rv, m4, K::mul(S, Pv)), K::fma(K::mul(rv, v), m4, K::mul(Pv, Pv)));
+    };
     if (STENCIL >= 18 && C.ck[3] != T(0)) {
-        // shell 2: (1,1,0), (0,1,1), (1,0,1), (1,-1,0), (0,1,-1), (1,0,-1)
+        // shell 2: (1,+-1,0), (0,1,+-1), (1,0,+-1): x, y = t_i, t_j and x', y' = t_i t_j, 1
         P n2 = zero, d2 = one;
-        auto pair = [&](P x, P y) {
-            const P xy = K::mul(x, y);
-            const P np = K::add(x, y), dp = K::add(one, xy);
-            const P nm = K::sub(x, y), dm = K::sub(one, xy);
-            const P np2 = K::mul(np, np), nm2 = K::mul(nm, nm);
-            acc(n2, d2, np2, K::fma(np2, neg_u, K::mul(dp, dp)));
-            acc(n2, d2, nm2, K::fma(nm2, neg_u, K::mul(dm, dm)));
-        };
-        pair(a, b);
-        pair(b, c);
-        pair(a, c);
-        acc(num, den, K::mul(K::mk(T(-4) * C.dt * C.ck[3], T(-4) * C.dt * C.ck[3]), n2), d2);
+        const P ab = K::mul(a2, b2), bc = K::mul(b2, c2), ac = K::mul(a2, c2);
+        pair(n2, d2, K::add(a2, b2), K::add(one, ab), ab);
+        pair(n2, d2, K::add(b2, c2), K::add(one, bc), bc);
+        pair(n2, d2, K::add(a2, c2), K::add(one, ac), ac);
+        acc(num, den, K::mul(K::mk(T(-8) * C.dt * C.ck[3], T(-8) * C.dt * C.ck[3]), n2), d2);
     }
     if (STENCIL >= 26 && C.ck[9] != T(0)) {
-        // shell 3: (1,1,1), (-1,1,1), (1,-1,1), (1,1,-1):
-        // tanh(x + y + z) = (tx + ty + tz + tx ty tz) / (1 + tx ty + ty tz + tx tz)
-        const P ab = K::mul(a, b), bc = K::mul(b, c), ca = K::mul(c, a), abc = K::mul(ab, c);
+        // shell 3: tanh(x + y + z) = (tx + ty + tz + tx ty tz) / (1 + tx ty + ty tz + tx tz).
+        // (1,1,+-1): N = al +- tz be, D = be +- tz al with al = tx + ty, be = 1 + tx ty;
+        // (-1,1,1), (1,-1,1): the same with al = ty - tx, be = 1 - tx ty.
         P n3 = zero, d3 = one;
-        auto term = [&](P N, P D) {
-            const P N2 = K::mul(N, N);
-            acc(n3, d3, N2, K::fma(N2, neg_u, K::mul(D, D)));
-        };
-        term(K::add(K::add(a, b), K::add(c, abc)), K::add(K::add(one, ab), K::add(bc, ca)));
-        term(K::sub(K::add(b, c), K::add(a, abc)), K::sub(K::add(one, bc), K::add(ab, ca)));
-        term(K::sub(K::add(a, c), K::add(b, abc)), K::sub(K::add(one, ca), K::add(ab, bc)));
-        term(K::sub(K::add(a, b), K::add(c, abc)), K::sub(K::add(one, ab), K::add(bc, ca)));
-        acc(num, den, K::mul(K::mk(T(-4) * C.dt * C.ck[9], T(-4) * C.dt * C.ck[9]), n3), d3);
+        const P ab = K::mul(a, b);
+        const P al1 = K::add(a, b), be1 = K::add(one, ab);
+        const P al2 = K::sub(b, a), be2 = K::sub(one, ab);
+        const P A1 = K::mul(al1, al1), B1 = K::mul(be1, be1);
+        const P A2 = K::mul(al2, al2), B2 = K::mul(be2, be2);
+        pair(n3, d3, K::fma(c2, B1, A1), K::fma(c2, A1, B1), K::mul(K::mul(A1, B1), c2));
+        pair(n3, d3, K::fma(c2, B2, A2), K::fma(c2, A2, B2), K::mul(K::mul(A2, B2), c2));
+        acc(num, den, K::mul(K::mk(T(-8) * C.dt * C.ck[9], T(-8) * C.dt * C.ck[9]), n3), d3);
     }
     const P nkmu = K::mk(-C.dt * C.kmu, -C.dt * C.kmu);
     const P w = K::fma(sg, K::div(num, den), nkmu);
