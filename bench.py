@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64", "bf16"])
     ap.add_argument("--scheme", default="ti120", choices=["ti120", "fd", "local"])
     ap.add_argument("--no-variants", action="store_true", help="skip the TI_n / CF timings")
+    ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-storage leg")
     ap.add_argument("--n", type=int, default=512, help="grid edge")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -260,6 +261,8 @@ def batched_vs_plain(n_grids: int, dev):
         cells = sum(j["nx"] * j["ny"] * j["nz"] for j in jobs)
         b = S.Batch(grids, stream=stream)
         b.step(16, args)
+        # work-list depth chosen by the autotuner (its trial steps are real steps)
+        depth, depth_ms = b.autotune(args, steps_per_trial=32)
         for g, a in zip(grids, args):
             g.step(2, lam=a.lam, dt=a.dt, dF=a.dF, stencil=26)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -294,7 +297,55 @@ def batched_vs_plain(n_grids: int, dev):
             "speedup": batched / plain, "velocity_rel_err_median": float(np.median(errs)),
             "velocity_rel_err_p90": float(np.percentile(errs, 90)),
             "velocity_rel_err_max": float(errs.max()),
+            "depth": depth, "depth_ms_per_step": {str(k): v for k, v in depth_ms.items()},
             "note": "batched and plain give bit-identical fields (tests/test_gpu_batch.py)"}
+
+
+def bf16_variant(w, dev, steps: int = 100):
+    """BF16 storage with FP32 arithmetic: the step rate of the default workload
+    (4 B per update) and the acceptance check, the planar velocity error of a
+    tilted 96x64x64 job against v_th = -M dF/Gamma next to the same job in FP32
+    (accepted when it holds the 1e-4 bar)."""
+    import torch
+    from paper_1910_05180_gb300 import spfm as S
+    stream = torch.cuda.Stream(device=dev)
+    out = {}
+    with torch.cuda.stream(stream):
+        g = S.Grid(w["nx"], w["ny"], w["nz"], dtype=S.SPFM_BF16, bc=(S.SPFM_PERIODIC,) * 6, n=w["u"],
+                   center=w["ctr"], stream=stream)
+        g.init_sphere(w["ctr"], w["R"], w["lam"], w["dx"])
+        kw = dict(lam=w["lam"], dx=w["dx"], dt=w["dt"], dF=w["dF"], stencil=26, scheme=S.SPFM_TI_GLOBAL)
+        g.step(5, **kw)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        g.step(steps, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        cells = w["nx"] * w["ny"] * w["nz"]
+        peak, _ = measured_hbm_peak()
+        out["cell_updates_per_s"] = cells / (ms / 1e3)
+        out["ms_per_step"] = ms
+        out["frac_hbm"] = cells * 4 / (ms / 1e3) / 1e9 / peak
+        g.close()
+        n = (1.0 / 3 ** 0.5,) * 3
+        shape = (96, 64, 64)
+        c = float(np.dot(n, (np.array(shape) - 1) / 2.0))
+        for name, dt_ in (("f32", S.SPFM_F32), ("bf16", S.SPFM_BF16)):
+            h = S.Grid(*shape, dtype=dt_, bc=(S.SPFM_CONTACT,) * 6, n=n, stream=stream)
+            h.init_planar(c, 3.0)
+            a = dict(lam=3.0, dt=0.05, dF=0.05, stencil=26, scheme=S.SPFM_TI_GLOBAL)
+            h.step(1000, **a)
+            p1 = h.stats()["position"]
+            h.step(1000, **a)
+            p2 = h.stats()["position"]
+            v = (p2 - p1) / (1000 * 0.05)
+            out[f"planar_velocity_rel_err_{name}"] = abs(v / -0.05 - 1.0)
+            h.close()
+    out["accepted"] = bool(out["planar_velocity_rel_err_bf16"] <= 1e-4)
+    out["workload"] = w["name"] + "_ti120_bf16_27pt"
+    return out
 
 
 def serving_run(n_jobs: int):
@@ -409,6 +460,10 @@ def run_gpu(args):
             variants[name] = {"cell_updates_per_s": cells / (ms / 1e3), "ms_per_step": ms,
                               "frac_hbm": cells * bpu / (ms / 1e3) / 1e9 / peak}
 
+    bf16 = None
+    if rank == 0 and not args.no_bf16 and args.dtype != "bf16":
+        bf16 = bf16_variant(w, dev)
+
     # end to end through the public API from pinned host memory: upload the
     # initial field, E2E_STEPS steps, stats, read the field back
     e2e = None
@@ -466,7 +521,7 @@ def run_gpu(args):
                          "avg_launch_ms": avg_kernel_ms,
                          "timed": "per step: stencil kernel + ghost-face kernel (events around 50-step chunks)"},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
-            "batched": batched, "serving": serving, "grain_sphericity": grain, "variants": variants,
+            "batched": batched, "serving": serving, "grain_sphericity": grain, "variants": variants, "bf16_storage": bf16,
             "last_stats": stats_seen[-1] if stats_seen else None,
             "stats_call": {"ms": (total_ms - step_ms) / max(1, len(stats_seen)), "every": STATS_EVERY,
                            "note": "interface stats between step chunks, host round trip included"},

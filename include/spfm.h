@@ -183,6 +183,18 @@ spfm_status spfm_batch_create(spfm_grid *const *grids, int n, void *scratch,
 /* n_steps steps of every grid with its own args[i]; all grids must share stencil and
  * scheme.  Replays a captured CUDA graph of the per-step launches. */
 spfm_status spfm_batch_step(spfm_batch *b, int n_steps, const spfm_step_args *args);
+/* Autotuner of the batch's work-list: the z-march depth of its items (planes
+ * per item: 8, 12, 16, 24, 32, 48 or 64).  Each candidate is timed with CUDA
+ * events over steps_per_trial steps (a multiple of 16, at least 16) after a
+ * 16-step warm-up, all of them real steps of every grid with args, exactly as
+ * spfm_batch_step would take them: the grids advance by 7 * (16 + steps_per_trial)
+ * steps in all, and their fields do not depend on the depth chosen.  The
+ * fastest depth is kept for later steps.  Needs a non-default stream (graphs).
+ * out_depth (may be NULL) receives the depth chosen, out_ms (may be NULL, else
+ * 7 doubles) the milliseconds per step of each candidate in the order above.
+ * Synchronises the stream.  No counterpart in the paper. */
+spfm_status spfm_batch_autotune(spfm_batch *b, const spfm_step_args *args, int steps_per_trial,
+                                int *out_depth, double *out_ms);
 /* Diagnostics of every grid in one pass; out has n entries.  Synchronises. */
 spfm_status spfm_batch_stats(spfm_batch *b, int flags, spfm_stats *out);
 spfm_status spfm_batch_destroy(spfm_batch *b);

@@ -20,8 +20,12 @@ using namespace spfm_host;
 
 namespace {
 
-constexpr int kBatchZChunk = 32;
-constexpr int kGraphSteps = 16;   // steps per captured graph (even: parity repeats)
+constexpr int kBatchZChunk = 32;   // z-march depth of the items until tuned
+constexpr int kGraphSteps = 16;    // steps per captured graph (even: parity repeats)
+// depths the autotuner tries; the scratch holds the work-list of the shallowest
+constexpr int kDepths[] = {8, 12, 16, 24, 32, 48, 64};
+constexpr int kNDepths = (int)(sizeof(kDepths) / sizeof(kDepths[0]));
+constexpr int kMinDepth = 8;
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -35,11 +39,11 @@ size_t grid_record_bytes(int dtype)
                              : (dtype == SPFM_F32 ? batch_grid_bytes_f32() : batch_grid_bytes_bf16());
 }
 
-int items_of(int dtype, const GridGeom &g, int gi, BatchItem *out)
+int items_of(int dtype, const GridGeom &g, int gi, int depth, BatchItem *out)
 {
-    return dtype == SPFM_F64   ? batch_items_f64(g, gi, kBatchZChunk, out)
-           : dtype == SPFM_F32 ? batch_items_f32(g, gi, kBatchZChunk, out)
-                               : batch_items_bf16(g, gi, kBatchZChunk, out);
+    return dtype == SPFM_F64   ? batch_items_f64(g, gi, depth, out)
+           : dtype == SPFM_F32 ? batch_items_f32(g, gi, depth, out)
+                               : batch_items_bf16(g, gi, depth, out);
 }
 
 Layout layout_for(int dtype, int n, int nitems)
@@ -74,10 +78,10 @@ int check_grids(spfm_grid *const *grids, int n, int *dtype, int *nitems)
             return fail(nullptr, SPFM_EINVAL, "spfm_batch: grid %d has another dtype", i);
         for (int j = 0; j < i; ++j)
             if (grids[j] == grids[i]) return fail(nullptr, SPFM_EINVAL, "spfm_batch: grid %d repeated", i);
-        items += items_of(grids[i]->d.dtype, grids[i]->geom, i, nullptr);
+        items += items_of(grids[i]->d.dtype, grids[i]->geom, i, kMinDepth, nullptr);
     }
     *dtype = grids[0]->d.dtype;
-    *nitems = items;
+    *nitems = items;   // the longest work-list (shallowest depth): the scratch size
     return SPFM_OK;
 }
 
@@ -85,7 +89,7 @@ int check_grids(spfm_grid *const *grids, int n, int *dtype, int *nitems)
 
 struct spfm_batch {
     std::vector<spfm_grid *> grids;
-    int n = 0, dtype = 0, nitems = 0;
+    int n = 0, dtype = 0, nitems = 0, depth = kBatchZChunk;
     char *scratch = nullptr;
     cudaStream_t stream = nullptr;
     Layout L;
@@ -107,6 +111,25 @@ static int bfail(spfm_batch *b, int code, const char *msg)
 {
     if (b) b->err = msg;
     return fail(nullptr, code, "%s", msg);
+}
+
+// the work-list of z-march depth `depth`, uploaded on the batch's stream (the
+// captured graph holds the item count, so it is dropped)
+static cudaError_t set_depth(spfm_batch *b, int depth)
+{
+    int k = 0;
+    for (int i = 0; i < b->n; ++i) k += items_of(b->dtype, b->grids[i]->geom, i, depth, nullptr);
+    b->h_items.resize(k);
+    k = 0;
+    for (int i = 0; i < b->n; ++i) k += items_of(b->dtype, b->grids[i]->geom, i, depth, b->h_items.data() + k);
+    b->nitems = k;
+    b->depth = depth;
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    return cudaMemcpyAsync(b->scratch + b->L.items, b->h_items.data(), sizeof(BatchItem) * k,
+                           cudaMemcpyHostToDevice, b->stream);
 }
 
 // one step of every grid: persistent step kernel, then the ghost faces of the
@@ -181,15 +204,11 @@ spfm_status spfm_batch_create(spfm_grid *const *grids, int n, void *scratch, siz
     b->scratch = (char *)scratch;
     b->stream = (cudaStream_t)stream;
     b->L = L;
-    b->h_items.resize(nitems);
-    int k = 0;
-    for (int i = 0; i < n; ++i) k += items_of(dtype, grids[i]->geom, i, b->h_items.data() + k);
     b->h_grids.assign(grid_record_bytes(dtype) * n, 0);
     b->h_ghosts.resize(n);
     b->h_stats.resize(n);
     b->h_finals.resize((size_t)kNStat * n + 1);
-    cudaError_t e = cudaMemcpyAsync(b->scratch + L.items, b->h_items.data(), sizeof(BatchItem) * nitems,
-                                    cudaMemcpyHostToDevice, b->stream);
+    cudaError_t e = set_depth(b, kBatchZChunk);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->scratch + L.err, 0, 16, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
@@ -281,6 +300,56 @@ spfm_status spfm_batch_step(spfm_batch *b, int n_steps, const spfm_step_args *ar
         g->stencil = a.stencil;
         g->scheme = a.scheme;
     }
+    return SPFM_OK;
+}
+
+spfm_status spfm_batch_autotune(spfm_batch *b, const spfm_step_args *args, int steps_per_trial,
+                                int *out_depth, double *out_ms)
+{
+    if (!b || !args) return fail(nullptr, SPFM_EINVAL, "spfm_batch_autotune: NULL argument");
+    if (steps_per_trial < kGraphSteps || steps_per_trial % kGraphSteps)
+        return bfail(b, SPFM_EINVAL, "spfm_batch_autotune: steps_per_trial must be a positive multiple of 16");
+    if (!b->stream) return bfail(b, SPFM_EINVAL, "spfm_batch_autotune: needs a non-default stream");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return bfail(b, SPFM_ECUDA, cudaGetErrorString(e));
+    }
+    spfm_status st = SPFM_OK;
+    int best = kBatchZChunk;
+    double best_ms = 0.0;
+    for (int c = 0; c < kNDepths && st == SPFM_OK; ++c) {
+        e = set_depth(b, kDepths[c]);
+        if (e != cudaSuccess) {
+            st = bfail(b, SPFM_ECUDA, cudaGetErrorString(e));
+            break;
+        }
+        st = spfm_batch_step(b, kGraphSteps, args);   // captures this depth's graph, warms up
+        if (st != SPFM_OK) break;
+        e = cudaEventRecord(e0, b->stream);
+        if (e == cudaSuccess) st = spfm_batch_step(b, steps_per_trial, args);
+        if (e == cudaSuccess && st == SPFM_OK) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess && st == SPFM_OK) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess && st == SPFM_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) st = bfail(b, SPFM_ECUDA, cudaGetErrorString(e));
+        if (st != SPFM_OK) break;
+        const double per = (double)ms / steps_per_trial;
+        if (out_ms) out_ms[c] = per;
+        if (c == 0 || per < best_ms) {
+            best_ms = per;
+            best = kDepths[c];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SPFM_OK) return st;
+    e = set_depth(b, best);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, SPFM_ECUDA, cudaGetErrorString(e));
+    if (out_depth) *out_depth = best;
     return SPFM_OK;
 }
 

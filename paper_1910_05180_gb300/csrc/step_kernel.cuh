@@ -100,8 +100,14 @@ template <class T>
 struct PackCoef {
     using P = typename PackT<T>::P;
     P one, m2, m4, c1, c2, c3, ct, nkmu, nkap;
-    P nA[kMaxTerms], nbeta[kMaxTerms];
+    P nA[kMaxTerms], nbeta[kMaxTerms];   // -A_k and -beta_k dt of the coupling groups
     int nterms;
+    // the same pairs side by side (one 16- or 32-byte load each), read by the
+    // run-time group count path, whose coefficients may sit in global memory
+    struct __align__(2 * sizeof(P)) Pair {
+        P nA, nbeta;
+    };
+    Pair pair[kMaxTerms];
 };
 
 template <class T>
@@ -121,6 +127,8 @@ inline PackCoef<T> make_pack_coef(const StepCoef<T> &c)
     for (int k = 0; k < kMaxTerms; ++k) {
         p.nA[k] = PT::splat(-c.A[k]);
         p.nbeta[k] = PT::splat(c.nbetadt[k]);
+        p.pair[k].nA = p.nA[k];
+        p.pair[k].nbeta = p.nbeta[k];
     }
     p.nterms = c.nterms;
     return p;
@@ -602,39 +610,76 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
             for (int r = 0; r < RPT; ++r) {
                 if (gy + r >= g.ny || gx >= g.nx) continue;
                 T outv[VX];
+                if constexpr (KIND == 5) {
+                    // up to 13 groups counted at run time (in a batch the coefficients
+                    // sit in global memory): the running fraction over every pack of
+                    // the row per group, so that each (A, beta) pair is read once a row
+                    P acc[NP], sg[NP], q1[NP], u[NP], num[NP], den[NP];
+                    const typename PackCoef<T>::Pair t0 = PC.pair[0];
 #pragma unroll
-                for (int q = 0; q < NP; ++q) {
-                    const P ph = z[r].c[q];
-                    const P t = K::add(K::sub(m[r].c[q], ph), K::sub(p[r].c[q], ph));
-                    P acc = K::add(K::fma(PC.ct, t, ph), z[r].h[q]);      // phi + dt * Laplacian
-                    if (STENCIL != 6) acc = K::add(acc, K::add(m[r].g[q], p[r].g[q]));
-                    const P sg = K::fma(PC.m2, ph, PC.one);               // s = 1 - 2 phi
-                    const P q1 = K::mul(ph, K::sub(PC.one, ph));          // q = phi (1 - phi)
-                    P w;   // -dt (potential / q + 4 M dF / (lambda Gamma))
-                    if (KIND == 0) {
-                        w = K::fma(sg, PC.nkap, PC.nkmu);
-                    } else if (KIND == 6) {
-                        const P u = K::mul(sg, sg);
-                        const P s2 = K::mk(C.inv_2dx, C.inv_2dx);
-                        const P gz = K::mul(K::sub(p[r].psi[q], m[r].psi[q]), s2);
-                        w = ti_local_w<T, STENCIL>(C, sg, u, K::mul(z[r].gx[q], s2), K::mul(z[r].gy[q], s2), gz);
-                    } else {
-                        const P u = K::mul(sg, sg);
-                        P num = PC.nbeta[0];
-                        P den = K::fma(PC.nA[0], u, PC.one);
+                    for (int q = 0; q < NP; ++q) {
+                        const P ph = z[r].c[q];
+                        const P t = K::add(K::sub(m[r].c[q], ph), K::sub(p[r].c[q], ph));
+                        acc[q] = K::add(K::fma(PC.ct, t, ph), z[r].h[q]);
+                        if (STENCIL != 6) acc[q] = K::add(acc[q], K::add(m[r].g[q], p[r].g[q]));
+                        sg[q] = K::fma(PC.m2, ph, PC.one);
+                        q1[q] = K::mul(ph, K::sub(PC.one, ph));
+                        u[q] = K::mul(sg[q], sg[q]);
+                        num[q] = t0.nbeta;
+                        den[q] = K::fma(t0.nA, u[q], PC.one);
+                    }
 #pragma unroll
-                        for (int kk = 1; kk < NTMAX; ++kk) {
-                            if (KIND <= 4 || kk < PC.nterms) {
+                    for (int kk = 1; kk < NTMAX; ++kk) {
+                        if (kk < PC.nterms) {
+                            const typename PackCoef<T>::Pair tk = PC.pair[kk];
+#pragma unroll
+                            for (int q = 0; q < NP; ++q) {
+                                const P d = K::fma(tk.nA, u[q], PC.one);
+                                num[q] = K::fma(num[q], d, K::mul(tk.nbeta, den[q]));
+                                den[q] = K::mul(den[q], d);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) {
+                        const P o = K::fma(q1[q], K::fma(sg[q], K::div(num[q], den[q]), PC.nkmu), acc[q]);
+                        outv[2 * q] = o.x;
+                        outv[2 * q + 1] = o.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) {
+                        const P ph = z[r].c[q];
+                        const P t = K::add(K::sub(m[r].c[q], ph), K::sub(p[r].c[q], ph));
+                        P acc = K::add(K::fma(PC.ct, t, ph), z[r].h[q]);      // phi + dt * Laplacian
+                        if (STENCIL != 6) acc = K::add(acc, K::add(m[r].g[q], p[r].g[q]));
+                        const P sg = K::fma(PC.m2, ph, PC.one);               // s = 1 - 2 phi
+                        const P q1 = K::mul(ph, K::sub(PC.one, ph));          // q = phi (1 - phi)
+                        P w;   // -dt (potential / q + 4 M dF / (lambda Gamma))
+                        if (KIND == 0) {
+                            w = K::fma(sg, PC.nkap, PC.nkmu);
+                        } else if (KIND == 6) {
+                            const P s2 = K::mk(C.inv_2dx, C.inv_2dx);
+                            const P gz = K::mul(K::sub(p[r].psi[q], m[r].psi[q]), s2);
+                            w = ti_local_w<T, STENCIL>(C, sg, K::mul(sg, sg), K::mul(z[r].gx[q], s2),
+                                                       K::mul(z[r].gy[q], s2), gz);
+                        } else {
+                            // exactly KIND groups, coefficients from the parameter bank
+                            const P u = K::mul(sg, sg);
+                            P num = PC.nbeta[0];
+                            P den = K::fma(PC.nA[0], u, PC.one);
+#pragma unroll
+                            for (int kk = 1; kk < NTMAX; ++kk) {
                                 const P d = K::fma(PC.nA[kk], u, PC.one);
                                 num = K::fma(num, d, K::mul(PC.nbeta[kk], den));
                                 den = K::mul(den, d);
                             }
+                            w = K::fma(sg, K::div(num, den), PC.nkmu);
                         }
-                        w = K::fma(sg, K::div(num, den), PC.nkmu);
+                        const P o = K::fma(q1, w, acc);
+                        outv[2 * q] = o.x;
+                        outv[2 * q + 1] = o.y;
                     }
-                    const P o = K::fma(q1, w, acc);
-                    outv[2 * q] = o.x;
-                    outv[2 * q + 1] = o.y;
                 }
                 S *optr = obase + (long long)oz * g.plane + (long long)r * g.pitch;
                 if (gx + VX <= g.nx) {

@@ -97,6 +97,8 @@ SIGNATURES = [
     ("spfm_batch_scratch_bytes", _I, [ctypes.POINTER(_P), _I, ctypes.POINTER(ctypes.c_size_t)]),
     ("spfm_batch_create", _I, [ctypes.POINTER(_P), _I, _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
     ("spfm_batch_step", _I, [_P, _I, ctypes.POINTER(StepArgs)]),
+    ("spfm_batch_autotune", _I, [_P, ctypes.POINTER(StepArgs), _I, ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(ctypes.c_double)]),
     ("spfm_batch_stats", _I, [_P, _I, ctypes.POINTER(Stats)]),
     ("spfm_batch_destroy", _I, [_P]),
 ]
@@ -312,6 +314,17 @@ def spfm_batch_step(b, n_steps, args):
     _check(load().spfm_batch_step(b, int(n_steps), arr))
 
 
+BATCH_DEPTHS = (8, 12, 16, 24, 32, 48, 64)   # z-march depths the autotuner tries
+
+
+def spfm_batch_autotune(b, args, steps_per_trial=32):
+    arr = (StepArgs * len(args))(*args)
+    depth = ctypes.c_int(0)
+    ms = (ctypes.c_double * len(BATCH_DEPTHS))()
+    _check(load().spfm_batch_autotune(b, arr, int(steps_per_trial), ctypes.byref(depth), ms))
+    return depth.value, dict(zip(BATCH_DEPTHS, list(ms)))
+
+
 def spfm_batch_stats(b, n, flags=0, allow_nonfinite=False):
     arr = (Stats * n)()
     s = load().spfm_batch_stats(b, int(flags), arr)
@@ -347,6 +360,12 @@ class Batch:
 
     def step(self, n_steps, args):
         spfm_batch_step(self.handle, n_steps, args)
+
+    def autotune(self, args, steps_per_trial=32):
+        """Pick the work-list depth by timing each candidate on real steps (the
+        grids advance by len(BATCH_DEPTHS) * (16 + steps_per_trial) steps).
+        Returns (depth, {depth: ms per step})."""
+        return spfm_batch_autotune(self.handle, args, steps_per_trial)
 
     def stats(self, flags=0, allow_nonfinite=False):
         return spfm_batch_stats(self.handle, len(self.grids), flags, allow_nonfinite)

@@ -108,3 +108,25 @@ def test_batch_rejects_mixed_stencils():
         with pytest.raises(S.SpfmError) as e:
             b.step(1, args)
         assert e.value.status == S.SPFM_EINVAL
+
+
+def test_autotuned_batch_equals_single_grids_bitwise():
+    """The autotuner's trial steps are real steps, and the depth it picks
+    changes only the work-list: fields stay bit-identical to single grids."""
+    jobs = _jobs(5)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        batched = _grids(jobs, S.SPFM_F32, stream)
+        alone = _grids(jobs, S.SPFM_F32, stream)
+        b = S.Batch(batched, stream=stream)
+        args = _args(jobs)
+        depth, ms = b.autotune(args, steps_per_trial=16)
+        assert depth in S.BATCH_DEPTHS and all(v > 0.0 for v in ms.values())
+        tuned = len(S.BATCH_DEPTHS) * 32
+        b.step(21, args)
+        for g, a in zip(alone, args):
+            g.step(tuned + 21, lam=a.lam, dt=a.dt, dF=a.dF, stencil=26)
+        stream.synchronize()
+        for gb, ga in zip(batched, alone):
+            assert gb.stats()["steps"] == ga.stats()["steps"] == tuned + 21
+            assert torch.equal(gb.get_field(), ga.get_field())
