@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
     ap.add_argument("--serve-jobs", type=int, default=300)
     ap.add_argument("--sweep-grids", type=int, default=256)
+    ap.add_argument("--batch-only", action="store_true",
+                    help="only the batched sweep: build it, 32 + 64 steps, print its rate (a small "
+                         "command to profile the batch kernel)")
     return ap.parse_args()
 
 
@@ -533,10 +536,44 @@ def run_gpu(args):
     return 0
 
 
+def batch_only(n_grids: int):
+    """The batched orientation sweep alone at the default work-list depth: 32
+    warm-up steps, then 64 timed steps; prints one JSON line."""
+    import torch
+    from paper_1910_05180_gb300 import spfm as S
+    from paper_1910_05180_gb300 import workloads as WL
+    jobs = WL.orientation_sweep(n_grids=n_grids)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        grids = []
+        for j in jobs:
+            g = S.Grid(j["nx"], j["ny"], j["nz"], dtype=S.SPFM_F32, bc=(S.SPFM_CONTACT,) * 6, n=j["n"],
+                       stream=stream)
+            g.init_planar(j["c"], j["lam"])
+            grids.append(g)
+        args = [S.step_args(lam=j["lam"], dt=j["dt"], dF=j["dF"], stencil=26) for j in jobs]
+        cells = sum(j["nx"] * j["ny"] * j["nz"] for j in jobs)
+        b = S.Batch(grids, stream=stream)
+        b.step(32, args)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        b.step(64, args)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 64
+        b.close()
+    print(json.dumps({"workload": f"orientation_sweep_{n_grids}grids_f32_27pt", "cells": cells,
+                      "ms_per_step": ms, "cell_updates_per_s": cells / (ms / 1e3)}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch_only:
+        return batch_only(args.sweep_grids)
     return run_gpu(args)
 
 
