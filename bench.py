@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--scheme", default="ti120", choices=["ti120", "fd", "local"])
     ap.add_argument("--no-variants", action="store_true", help="skip the TI_n / CF timings")
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-storage leg")
+    ap.add_argument("--no-relax", action="store_true", help="skip the constant-volume shape relaxation")
     ap.add_argument("--n", type=int, default=512, help="grid edge")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -304,6 +305,39 @@ def batched_vs_plain(n_grids: int, dev):
             "note": "batched and plain give bit-identical fields (tests/test_gpu_batch.py)"}
 
 
+def shape_relaxation(dev):
+    """Sec. 3.3: a cubic particle (half side 12) in 60^3, periodic, relaxed at
+    constant volume by spfm_step_conserving for a fixed physical time (250),
+    then the residual anisotropy eps_eff of its phi = 1/2 contour (Fig. 9b) per
+    model and profile width lambda/dx, with the final volume-holding dF."""
+    import torch
+    from paper_1910_05180_gb300 import spfm as S
+    N = 60
+    ctr = ((N - 1) / 2.0,) * 3
+    u120 = tuple(np.array([1.0, 2.0, 0.0]) / np.sqrt(5.0))
+    out = {}
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        for lam, dt in ((4.0, 0.05), (2.0, 0.05), (1.3, 0.015)):
+            steps = int(round(250.0 / dt))
+            for name, sch in (("TI_n", S.SPFM_TI_LOCAL), ("TI_<120>", S.SPFM_TI_GLOBAL), ("CF", S.SPFM_FD)):
+                g = S.Grid(N, N, N, dtype=S.SPFM_F32, bc=(S.SPFM_PERIODIC,) * 6, n=u120, center=ctr,
+                           stream=stream)
+                g.init_cube(ctr, 12.0, lam)
+                v0 = g.stats()["volume"]
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                dF = g.step_conserving(steps, lam=lam, dt=dt, stencil=26, scheme=sch)
+                e1.record(stream)
+                sp = g.sphericity(0)
+                out[f"{name}_lam{lam:g}"] = {
+                    "eps_eff": sp["eps_eff"], "R_mean": sp["R_mean"], "dF": dF, "steps": steps, "dt": dt,
+                    "volume_rel_drift": abs(g.stats()["volume"] / v0 - 1.0),
+                    "ms_per_step": e0.elapsed_time(e1) / steps}
+                g.close()
+    return out
+
+
 def bf16_variant(w, dev, steps: int = 100):
     """BF16 storage with FP32 arithmetic: the step rate of the default workload
     (4 B per update) and the acceptance check, the planar velocity error of a
@@ -466,6 +500,9 @@ def run_gpu(args):
     bf16 = None
     if rank == 0 and not args.no_bf16 and args.dtype != "bf16":
         bf16 = bf16_variant(w, dev)
+    relax = None
+    if rank == 0 and not args.no_relax:
+        relax = shape_relaxation(dev)
 
     # end to end through the public API from pinned host memory: upload the
     # initial field, E2E_STEPS steps, stats, read the field back
@@ -524,7 +561,7 @@ def run_gpu(args):
                          "avg_launch_ms": avg_kernel_ms,
                          "timed": "per step: stencil kernel + ghost-face kernel (events around 50-step chunks)"},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
-            "batched": batched, "serving": serving, "grain_sphericity": grain, "variants": variants, "bf16_storage": bf16,
+            "batched": batched, "serving": serving, "grain_sphericity": grain, "variants": variants, "bf16_storage": bf16, "shape_relaxation": relax,
             "last_stats": stats_seen[-1] if stats_seen else None,
             "stats_call": {"ms": (total_ms - step_ms) / max(1, len(stats_seen)), "every": STATS_EVERY,
                            "note": "interface stats between step chunks, host round trip included"},

@@ -122,6 +122,13 @@ spfm_status spfm_init_planar(spfm_grid *g, double c, double lambda, double dx);
 spfm_status spfm_init_sphere(spfm_grid *g, const double ctr[3], double R, double lambda,
                              double dx);
 
+/* Cubic particle with phi = 0 inside, half side `half` around ctr: phi = 1 -
+ * prod_a (1 - tanh(2 (|p_a - ctr_a| - half)/lambda))/2, the start of the
+ * shape relaxation of Sec. 3.3 (the paper gives no cube profile; this product
+ * is the 1D ideal profile across each face away from edges and corners).  Also
+ * sets desc center = ctr. */
+spfm_status spfm_init_cube(spfm_grid *g, const double ctr[3], double half, double lambda, double dx);
+
 /* n_steps explicit steps (Eq. 2 with Eq. 1; TI per Eqs. 5-6, TI_n with the
  * local normal, or CF).  stencil in {6, 18, 26}.  Validates first:
  * SPFM_EINVAL, SPFM_EUNSTABLE (dt above 2 / bound of the Jacobian's spectral
@@ -129,6 +136,19 @@ spfm_status spfm_init_sphere(spfm_grid *g, const double ctr[3], double R, double
  * Sec. 3.1).  Asynchronous on the grid's stream. */
 spfm_status spfm_step(spfm_grid *g, int n_steps, double M, double Gamma, double lambda,
                       double dx, double dt, double dF, int stencil, int scheme);
+
+/* n_steps constant-volume steps (Sec. 3.3: a homogeneous, time-dependent
+ * driving force keeps the particle volume fixed).  Each step is spfm_step at
+ * dF = 0, then the one homogeneous dF for which the step leaves sum_p phi_p
+ * unchanged: with phi* the result at dF = 0, every cell loses alpha q(phi_p),
+ * alpha = sum_p (phi*_p - phi_p) / sum_p q(phi_p) (FP64 sums in a fixed order),
+ * which is dF = alpha lambda Gamma / (4 M dt) in the driving term of Eq. 2.
+ * Validation as spfm_step at dF = 0 (the phase-stability check of Sec. 3.1
+ * cannot see a dF decided during the run).  Uses the grid's scratch.
+ * dF_last (host pointer or NULL) receives the last step's dF; a non-NULL
+ * dF_last synchronises the stream. */
+spfm_status spfm_step_conserving(spfm_grid *g, int n_steps, double M, double Gamma, double lambda,
+                                 double dx, double dt, int stencil, int scheme, double *dF_last);
 
 /* FP64 interface diagnostics of the current field (Sec. 2.3 inversion of the
  * ideal profile); flags may include SPFM_STATS_ENERGY.  Uses the model of the

@@ -78,6 +78,10 @@ def _load():
             lib.oracle_rhs.restype = ctypes.c_long
             lib.oracle_step.argtypes = [P, dp, ctypes.c_int]
             lib.oracle_step.restype = ctypes.c_long
+            lib.oracle_step_conserving.argtypes = [P, dp, ctypes.c_int, dp]
+            lib.oracle_step_conserving.restype = ctypes.c_long
+            lib.oracle_init_cube.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_double]
             lib.oracle_stats.argtypes = [P, dp, dp, dp]
             lib.oracle_energy.argtypes = [P, dp]
             lib.oracle_energy.restype = ctypes.c_double
@@ -176,6 +180,16 @@ def init_sphere(p: Params, ctr, R: float) -> np.ndarray:
     return phi
 
 
+def init_cube(p: Params, ctr, half: float) -> np.ndarray:
+    """Cubic particle (phi = 0 inside) of half side `half`: the product of three
+    1D ideal profiles (the cube start of the Sec. 3.3 shape relaxation)."""
+    lib = _load()
+    phi = np.zeros(p.shape)
+    cc = np.ascontiguousarray(ctr, dtype=np.float64)
+    lib.oracle_init_cube(_dp(phi), p.nx, p.ny, p.nz, _dp(cc), half, p.lam, p.dx)
+    return phi
+
+
 def _field(p: Params, phi) -> np.ndarray:
     a = np.ascontiguousarray(phi, dtype=np.float64)
     assert a.shape == p.shape, (a.shape, p.shape)
@@ -199,6 +213,17 @@ def rhs(p: Params, phi):
     pc = p.c()
     nbad = lib.oracle_rhs(ctypes.byref(pc), _dp(a), _dp(R))
     return R, int(nbad)
+
+
+def step_conserving(p: Params, phi, n_steps: int):
+    """n_steps constant-volume steps (Sec. 3.3): each step's homogeneous dF is
+    the one that leaves sum(phi) unchanged.  Returns (field, dF per step)."""
+    lib = _load()
+    a = _field(p, phi).copy()
+    dF = np.zeros(max(int(n_steps), 1))
+    pc = p.c()
+    lib.oracle_step_conserving(ctypes.byref(pc), _dp(a), int(n_steps), _dp(dF))
+    return a, dF[:int(n_steps)]
 
 
 def step(p: Params, phi, n_steps: int) -> np.ndarray:

@@ -117,6 +117,20 @@ void oracle_init_sphere(double *phi, int nx, int ny, int nz, const double ctr[3]
             }
 }
 
+void oracle_init_cube(double *phi, int nx, int ny, int nz, const double ctr[3], double half,
+                      double lambda, double dx)
+{
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const double d[3] = {dx * i - ctr[0], dx * j - ctr[1], dx * k - ctr[2]};
+                double inside = 1.0;   /* product of the three 1D particle fractions */
+                for (int a = 0; a < 3; ++a)
+                    inside *= 0.5 * (1.0 - tanh(2.0 * (fabs(d[a]) - half) / lambda));
+                phi[((size_t)k * ny + j) * nx + i] = 1.0 - inside;
+            }
+}
+
 /* ---------------------------------------------------------------- ghosts */
 
 #define PADX(p) ((p)->nx + 2)
@@ -302,6 +316,31 @@ long oracle_step(const orc_params *p, double *phi, int n_steps)
     for (int s = 0; s < n_steps; ++s) {
         nbad += oracle_rhs(p, phi, R);
         for (size_t c = 0; c < n; ++c) phi[c] += p->dt * R[c];
+    }
+    free(R);
+    return nbad;
+}
+
+long oracle_step_conserving(const orc_params *p, double *phi, int n_steps, double *dF_out)
+{
+    size_t n = (size_t)p->nx * p->ny * p->nz;
+    double *R = (double *)malloc(sizeof(double) * n);
+    orc_params p0 = *p;
+    p0.dF = 0.0;
+    /* Eq. 2 with Eq. 1: the driving term of dphi/dt is -(2M/(3 lambda Gamma)) dF h3'(phi) */
+    const double pref = 2.0 * p->M / (3.0 * p->lambda * p->Gamma);
+    long nbad = 0;
+    for (int s = 0; s < n_steps; ++s) {
+        nbad += oracle_rhs(&p0, phi, R);
+        double sum_r = 0.0, sum_h = 0.0;
+        for (size_t c = 0; c < n; ++c) {
+            sum_r += R[c];
+            sum_h += h3_prime(phi[c]);
+        }
+        /* the homogeneous dF for which sum_p (R_p - pref dF h3'(phi_p)) = 0 */
+        const double dF = sum_h != 0.0 ? sum_r / (pref * sum_h) : 0.0;
+        for (size_t c = 0; c < n; ++c) phi[c] += p->dt * (R[c] - pref * dF * h3_prime(phi[c]));
+        if (dF_out) dF_out[s] = dF;
     }
     free(R);
     return nbad;

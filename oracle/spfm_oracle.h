@@ -23,6 +23,10 @@
  *   oracle_stats            exact on the ideal planar and radial profiles
  *   oracle_energy           shift invariance under TI, continuum limit
  *   oracle_contour          exact on planar ideal profiles (Sec. 2.3)
+ *   oracle_init_cube        closed form at face centres; a reading (the paper
+ *                           gives no cube profile)
+ *   oracle_step_conserving  sum phi invariant, zero dF on flat slabs,
+ *                           Gibbs-Thomson dF = 2 Gamma / R on a sphere
  */
 #ifndef SPFM_ORACLE_H
 #define SPFM_ORACLE_H
@@ -68,6 +72,13 @@ void oracle_init_planar(double *phi, int nx, int ny, int nz, const double n[3],
 void oracle_init_sphere(double *phi, int nx, int ny, int nz, const double ctr[3],
                         double R, double lambda, double dx);
 
+/* Cubic particle (phi = 0 inside) of half side `half` around ctr, the product
+ * of three 1D ideal profiles: phi = 1 - prod_a (1 - tanh(2 (|p_a - ctr_a| - half)/lambda))/2.
+ * The paper starts its shape relaxation (Sec. 3.3) from a cube without giving
+ * the profile; this product is exact across every face away from edges. */
+void oracle_init_cube(double *phi, int nx, int ny, int nz, const double ctr[3], double half,
+                      double lambda, double dx);
+
 /* Copy phi into the padded array and fill the one-cell ghost layer,
  * faces x, then y, then z (so edges and corners compose). */
 void oracle_fill_ghosts(const orc_params *p, const double *phi, double *pad);
@@ -79,6 +90,14 @@ long oracle_rhs(const orc_params *p, const double *phi, double *R);
 
 /* n_steps explicit Euler steps phi <- phi + dt R (in place). */
 long oracle_step(const orc_params *p, double *phi, int n_steps);
+
+/* Constant-volume steps (Sec. 3.3: a homogeneous, time-dependent driving force
+ * keeps the particle volume fixed).  Each step takes R at dF = 0, then the one
+ * homogeneous dF for which the step leaves sum_p phi_p unchanged,
+ * dF = sum_p R_p / (2M/(3 lambda Gamma) sum_p h3'(phi_p)), and applies
+ * phi <- phi + dt (R - 2M/(3 lambda Gamma) dF h3'(phi)).  p->dF is ignored;
+ * dF_out (NULL or n_steps doubles) receives each step's dF. */
+long oracle_step_conserving(const orc_params *p, double *phi, int n_steps, double *dF_out);
 
 /* FP64 interface diagnostics (Sec. 2.3 inversion of the ideal profile):
  * out[0] volume sum(phi) dx^3, out[1] S_w = sum q, out[2] S_c, out[3] S_r,

@@ -343,9 +343,21 @@ spfm_status spfm_init_sphere(spfm_grid *g, const double ctr[3], double R, double
     if (!g || !ctr) return fail(g, SPFM_EINVAL, "spfm_init_sphere: NULL argument");
     InitArgs a;
     memset(&a, 0, sizeof a);
-    a.sphere = 1;
+    a.shape = 1;
     for (int i = 0; i < 3; ++i) { a.ctr[i] = ctr[i]; g->d.center[i] = ctr[i]; }
     a.R = R;
+    return init_common(g, a, lambda, dx);
+}
+
+spfm_status spfm_init_cube(spfm_grid *g, const double ctr[3], double half, double lambda, double dx)
+{
+    if (!g || !ctr) return fail(g, SPFM_EINVAL, "spfm_init_cube: NULL argument");
+    if (!(half > 0.0)) return fail(g, SPFM_EINVAL, "spfm_init_cube: half side must be > 0");
+    InitArgs a;
+    memset(&a, 0, sizeof a);
+    a.shape = 2;
+    for (int i = 0; i < 3; ++i) { a.ctr[i] = ctr[i]; g->d.center[i] = ctr[i]; }
+    a.half = half;
     return init_common(g, a, lambda, dx);
 }
 
@@ -405,6 +417,69 @@ spfm_status spfm_step(spfm_grid *g, int n_steps, double M, double Gamma, double 
     g->dF = dF;
     g->stencil = stencil;
     g->scheme = scheme;
+    return SPFM_OK;
+}
+
+spfm_status spfm_step_conserving(spfm_grid *g, int n_steps, double M, double Gamma, double lambda, double dx,
+                                 double dt, int stencil, int scheme, double *dF_last)
+{
+    if (!g) return fail(nullptr, SPFM_EINVAL, "spfm_step_conserving: grid is NULL");
+    if (n_steps < 0) return fail(g, SPFM_EINVAL, "spfm_step_conserving: n_steps < 0");
+    Model m;
+    spfm_status st = build_model(g, M, Gamma, lambda, dx, dt, 0.0, stencil, scheme, m);
+    if (st != SPFM_OK) return st;
+    const LaunchCfg cfg{stencil, scheme};
+    cudaStream_t s = stream_of(g);
+    if (n_steps > 0 && (g->ghosts_dirty || g->ghost_lambda != lambda || g->ghost_dx != dx)) {
+        st = refresh_ghosts(g, lambda, dx);
+        if (st != SPFM_OK) return st;
+    }
+    int *err = err_word(g);
+    double *partials = (double *)g->d.scratch;
+    double *alpha = (double *)((char *)g->d.scratch + scratch_final_offset());
+    StepCoef<double> cd;
+    StepCoef<float> cf;
+    if (g->d.dtype == SPFM_F64) {
+        fill_coef<double>(g, m, dt, stencil, cd);
+        set_local_coef<double>(cd, lambda, dx);
+    } else {
+        fill_coef<float>(g, m, dt, stencil, cf);
+        set_local_coef<float>(cf, lambda, dx);
+    }
+    for (int i = 0; i < n_steps; ++i) {
+        void *src = g->d.field[g->cur], *dst = g->d.field[1 - g->cur];
+        cudaError_t e;
+        if (g->d.dtype == SPFM_F64)
+            e = launch_step_f64(cd, (const double *)src, (double *)dst, err, cfg, &g->tma, g->cur, s);
+        else if (g->d.dtype == SPFM_F32)
+            e = launch_step_f32(cf, (const float *)src, (float *)dst, err, cfg, &g->tma, g->cur, s);
+        else
+            e = launch_step_bf16(cf, (const __nv_bfloat16 *)src, (__nv_bfloat16 *)dst, err, cfg, &g->tma,
+                                 g->cur, s);
+        if (e == cudaSuccess) e = launch_conserve(g->geom, g->d.dtype, src, dst, partials, alpha, s);
+        if (e == cudaSuccess) e = launch_fill_ghosts(g->geom, g->d.dtype, m.aface, dst, s, 1);
+        if (e != cudaSuccess) return cuda_fail(g, e, "spfm_step_conserving");
+        g->cur ^= 1;
+    }
+    g->steps += n_steps;
+    g->time += n_steps * dt;
+    g->M = M;
+    g->Gamma = Gamma;
+    g->lambda = lambda;
+    g->dx = dx;
+    g->dF = 0.0;
+    g->stencil = stencil;
+    g->scheme = scheme;
+    if (dF_last) {
+        *dF_last = 0.0;
+        if (n_steps > 0) {
+            double a = 0.0;
+            cudaError_t e = cudaMemcpyAsync(&a, alpha, sizeof a, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return cuda_fail(g, e, "spfm_step_conserving");
+            *dF_last = a * lambda * Gamma / (4.0 * M * dt);
+        }
+    }
     return SPFM_OK;
 }
 

@@ -144,12 +144,18 @@ cudaError_t launch_step_bf16(const StepCoef<float> &c, const __nv_bfloat16 *src,
 struct InitArgs {
     GridGeom g;
     int dtype;
-    int sphere;           // 0 planar (n, c), 1 radial (ctr, R)
+    int shape;            // 0 planar (n, c), 1 radial (ctr, R), 2 cube (ctr, half)
     double n[3], c;
-    double ctr[3], R;
+    double ctr[3], R, half;
     double lambda, dx;
 };
 cudaError_t launch_init(const InitArgs &a, void *field, cudaStream_t st);
+
+// Constant-volume correction after a step at dF = 0 (conserve.cu): dst -=
+// alpha q(src) with alpha = sum(dst - src) / sum q(src); partials holds
+// 2 * kStatsBlocks doubles, alpha_out (device) receives alpha.
+cudaError_t launch_conserve(const GridGeom &g, int dtype, const void *src, void *dst, double *partials,
+                            double *alpha_out, cudaStream_t st);
 
 // Ghost layer of a buffer from its interior: all faces (x_faces = 1) or the y
 // and z faces only.  Face sizes must stay below 2^31 cells.

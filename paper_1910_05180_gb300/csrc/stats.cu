@@ -1,7 +1,8 @@
 // stats.cu -- ideal-profile initialisation and FP64 interface
 // diagnostics on the ghosted field layout (spfm_internal.h).
 //
-// init: Eq. 3 (planar) or its radial form, evaluated in FP64 per cell and
+// init: Eq. 3 (planar), its radial form, or a cube as the product of three 1D
+// profiles (the start of the Sec. 3.3 shape relaxation), evaluated in FP64 per cell and
 // rounded once to the storage type (the caller then fills the ghost layer).
 //
 // stats: one pass over the interior with FP64 sums, per lane in a fixed
@@ -51,10 +52,16 @@ __global__ void init_kernel(const InitArgs a, S *f)
             double v = 0.0;
             if (inner && i >= 0 && i < a.g.nx) {
                 const double px = a.dx * i, py = a.dx * j, pz = a.dx * k;
-                if (a.sphere) {
+                if (a.shape == 1) {
                     const double rx = px - a.ctr[0], ry = py - a.ctr[1], rz = pz - a.ctr[2];
                     const double rr = sqrt(rx * rx + ry * ry + rz * rz);
                     v = 0.5 * (1.0 - tanh(2.0 * (a.R - rr) / a.lambda));
+                } else if (a.shape == 2) {
+                    // cube: product of the three 1D particle fractions
+                    const double d[3] = {px - a.ctr[0], py - a.ctr[1], pz - a.ctr[2]};
+                    double inside = 1.0;
+                    for (int ax = 0; ax < 3; ++ax) inside *= 0.5 * (1.0 - tanh(2.0 * (fabs(d[ax]) - a.half) / a.lambda));
+                    v = 1.0 - inside;
                 } else {
                     const double pn = px * a.n[0] + py * a.n[1] + pz * a.n[2];
                     v = 0.5 * (1.0 - tanh(2.0 * (pn - a.c) / a.lambda));

@@ -86,7 +86,9 @@ SIGNATURES = [
     ("spfm_set_stream", _I, [_P, _P]),
     ("spfm_init_planar", _I, [_P, _D, _D, _D]),
     ("spfm_init_sphere", _I, [_P, ctypes.POINTER(_D), _D, _D, _D]),
+    ("spfm_init_cube", _I, [_P, ctypes.POINTER(_D), _D, _D, _D]),
     ("spfm_step", _I, [_P, _I, _D, _D, _D, _D, _D, _D, _I, _I]),
+    ("spfm_step_conserving", _I, [_P, _I, _D, _D, _D, _D, _D, _I, _I, ctypes.POINTER(_D)]),
     ("spfm_interface_stats", _I, [_P, _I, ctypes.POINTER(Stats)]),
     ("spfm_interface_stats_static", _I, [ctypes.POINTER(GridDesc), _P, _D, _D, ctypes.POINTER(Stats)]),
     ("spfm_sphericity", _I, [_P, _I, ctypes.POINTER(_D)]),
@@ -161,8 +163,20 @@ def spfm_init_sphere(h, ctr, R, lam, dx):
     _check(load().spfm_init_sphere(h, arr, R, lam, dx), h)
 
 
+def spfm_init_cube(h, ctr, half, lam, dx):
+    arr = (ctypes.c_double * 3)(*ctr)
+    _check(load().spfm_init_cube(h, arr, half, lam, dx), h)
+
+
 def spfm_step(h, n_steps, M, Gamma, lam, dx, dt, dF, stencil, scheme):
     _check(load().spfm_step(h, int(n_steps), M, Gamma, lam, dx, dt, dF, int(stencil), int(scheme)), h)
+
+
+def spfm_step_conserving(h, n_steps, M, Gamma, lam, dx, dt, stencil, scheme):
+    dF = ctypes.c_double(0.0)
+    _check(load().spfm_step_conserving(h, int(n_steps), M, Gamma, lam, dx, dt, int(stencil), int(scheme),
+                                       ctypes.byref(dF)), h)
+    return dF.value
 
 
 def spfm_interface_stats(h, flags=0, allow_nonfinite=False) -> dict:
@@ -257,9 +271,17 @@ class Grid:
     def init_sphere(self, ctr, R, lam, dx=1.0):
         spfm_init_sphere(self.handle, ctr, R, lam, dx)
 
+    def init_cube(self, ctr, half, lam, dx=1.0):
+        spfm_init_cube(self.handle, ctr, half, lam, dx)
+
     def step(self, n_steps, M=1.0, Gamma=1.0, lam=4.0, dx=1.0, dt=0.1, dF=0.0, stencil=26,
              scheme=SPFM_TI_GLOBAL):
         spfm_step(self.handle, n_steps, M, Gamma, lam, dx, dt, dF, stencil, scheme)
+
+    def step_conserving(self, n_steps, M=1.0, Gamma=1.0, lam=4.0, dx=1.0, dt=0.1, stencil=26,
+                        scheme=SPFM_TI_GLOBAL):
+        """Constant-volume steps (Sec. 3.3); returns the last step's dF."""
+        return spfm_step_conserving(self.handle, n_steps, M, Gamma, lam, dx, dt, stencil, scheme)
 
     def stats(self, flags=0, allow_nonfinite=False) -> dict:
         return spfm_interface_stats(self.handle, flags, allow_nonfinite)

@@ -410,3 +410,61 @@ def test_local_normal_equals_global_on_planar_profile():
         assert np.abs(Rl - Rg)[ok].max() < 1e-11
         if (~ok).any():
             assert np.abs(Rl - Rg)[~ok].max() < 1e-4
+
+
+# ------------------------------------------------ constant-volume relaxation
+
+
+def test_cube_profile_is_the_1d_profile_across_each_face():
+    """The cube start: far from edges the product of the three 1D fractions is
+    the 1D ideal profile (Eq. 3) across the face; the cube has its symmetries."""
+    N, lam, half = 40, 3.0, 10.0
+    p = O.Params(N, N, N, lam=lam)
+    ctr = ((N - 1) / 2.0,) * 3
+    phi = O.init_cube(p, ctr, half)
+    j = k = N // 2   # the line through the face centres along x (|dy|, |dz| = 0.5)
+    x = np.arange(N) - ctr[0]
+    inner = (1 - np.tanh(2 * (0.5 - half) / lam)) / 2   # the other two factors
+    want = 1 - inner ** 2 * (1 - np.tanh(2 * (np.abs(x) - half) / lam)) / 2
+    assert np.abs(phi[k, j, :] - want).max() < 1e-14
+    assert np.abs(phi - phi.transpose(0, 2, 1)).max() < 1e-14
+    assert np.abs(phi - phi[::-1, :, :]).max() < 1e-14
+
+
+@pytest.mark.parametrize("scheme", [O.CF, O.TI_LOCAL, O.TI_GLOBAL])
+def test_conserving_step_keeps_sum_phi(scheme):
+    """Sec. 3.3: the homogeneous driving force holds the particle volume, so
+    sum(phi) is invariant step after step (rounding only), while the field
+    itself does change."""
+    N = 24
+    p = O.Params(N, N, N, n=tuple(_unit([1, 2, 0])), lam=2.5, dt=0.05, stencil=26, scheme=scheme)
+    rng = np.random.default_rng(3)
+    phi0 = O.init_cube(p, ((N - 1) / 2.0,) * 3, 6.0) + 0.01 * rng.random(p.shape)
+    phi, dF = O.step_conserving(p, phi0, 30)
+    assert abs(phi.sum() - phi0.sum()) <= 1e-12 * phi0.sum()
+    assert np.abs(phi - phi0).max() > 1e-3 and np.all(np.isfinite(dF))
+
+
+def test_conserving_step_needs_no_force_on_an_exact_plane():
+    """An ideal planar interface under TI with contact faces is a fixed point
+    (Eq. 4) at dF = 0, so the volume-holding dF is zero and nothing moves."""
+    n = _unit([1, 2, 2])
+    p = O.Params(24, 20, 18, bc=(O.CONTACT,) * 6, n=tuple(n), lam=3.0, dt=0.05, stencil=26)
+    phi0 = O.init_planar(p, float(n @ [11.5, 9.5, 8.5]))
+    phi, dF = O.step_conserving(p, phi0, 20)
+    assert np.abs(dF).max() < 1e-13
+    assert np.abs(phi - phi0).max() < 1e-13
+
+
+def test_conserving_force_on_a_sphere_is_gibbs_thomson():
+    """Sharp-interface limit: the force that holds a sphere of radius R is the
+    curvature force 2 Gamma / R, independent of the mobility M, with an error
+    of order (lambda/R)^2 (it falls about fourfold when R doubles)."""
+    errs = []
+    for R, N in ((12.0, 40), (24.0, 64)):
+        for M, G in ((1.0, 1.0), (3.0, 2.0)):
+            p = O.Params(N, N, N, lam=3.0, dt=0.02, stencil=26, n=(1.0, 0.0, 0.0), M=M, Gamma=G)
+            _, dF = O.step_conserving(p, O.init_sphere(p, ((N - 1) / 2.0,) * 3, R), 1)
+            errs.append(abs(dF[0] / (2 * G / R) - 1))
+    assert abs(errs[0] - errs[1]) < 1e-12 and abs(errs[2] - errs[3]) < 1e-12
+    assert errs[0] < 0.015 and errs[2] < 0.004 and errs[0] > 3.0 * errs[2]
