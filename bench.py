@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-variants", action="store_true", help="skip the TI_n / CF timings")
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-storage leg")
     ap.add_argument("--no-relax", action="store_true", help="skip the constant-volume shape relaxation")
+    ap.add_argument("--no-friction", action="store_true", help="skip the 1D friction study")
     ap.add_argument("--n", type=int, default=512, help="grid edge")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -305,6 +306,73 @@ def batched_vs_plain(n_grids: int, dev):
             "note": "batched and plain give bit-identical fields (tests/test_gpu_batch.py)"}
 
 
+def friction_1d(dev, steps: int = 24000, window: int = 200):
+    """Sec. 3.1, Fig. 8: stationary velocity of a planar interface in 1D
+    (64 x 1 x 1, no-flux in x, 27-point weights) against v_th = -M dF/Gamma,
+    for CF + h3, CF + h5, CF + h_Abel and TI + h3 at lambda~ = 4, 3, 2.5 over a
+    range of dF~.  All runs of one model step together as one batch; the frame
+    moves back one cell whenever the favoured phase fills half the system
+    (spfm_shift_x).  dt = min(0.002 / dF~, dt_max / 2) keeps the interface's
+    advance per step at 0.002 cells where stability allows.  The velocity is the
+    slope of the fixed-frame position over the last 60 % of the run; the
+    oscillation is the spread of the window velocities.  Reduced step counts:
+    the paper's runs take 2.5e8 steps at a far finer dt."""
+    import torch
+    from paper_1910_05180_gb300 import spfm as S
+    models = (("CF+h3", S.SPFM_FD), ("CF+h5", S.SPFM_FD_H5), ("CF+h_Abel", S.SPFM_FD_HABEL),
+              ("TI+h3", S.SPFM_TI_GLOBAL))
+    lams = (4.0, 3.0, 2.5)
+    dFs = (0.002, 0.005, 0.01, 0.02, 0.05, 0.1, 0.2, 0.5)
+    nx = 64
+    bc = (S.SPFM_NOFLUX, S.SPFM_NOFLUX) + (S.SPFM_PERIODIC,) * 4
+    out = {}
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        for name, sch in models:
+            res = {f"lam{lam:g}": {} for lam in lams}
+            grids, args, runs = [], [], []
+            for lam in lams:
+                for dF in dFs:
+                    g = S.Grid(nx, 1, 1, dtype=S.SPFM_F64, bc=bc, n=(1.0, 0.0, 0.0), stream=stream)
+                    try:
+                        dt = min(0.002 / dF, 0.5 * g.max_dt(lam=lam, dF=dF, stencil=26, scheme=sch))
+                    except S.SpfmError as e:
+                        res[f"lam{lam:g}"][f"{dF:g}"] = "phase unstable" if e.status == S.SPFM_EPHASE else str(e)
+                        g.close()
+                        continue
+                    g.init_planar((nx - 1) / 2.0, lam)
+                    grids.append(g)
+                    args.append(S.step_args(lam=lam, dt=dt, dF=dF, stencil=26, scheme=sch))
+                    runs.append((lam, dF, dt))
+            b = S.Batch(grids, stream=stream)
+            offset = np.zeros(len(grids))
+            pos = [[] for _ in grids]
+            nwin = steps // window
+            for w in range(nwin):
+                b.step(window, args)
+                st = b.stats()
+                for i, (g, sti) in enumerate(zip(grids, st)):
+                    if w >= int(0.4 * nwin):
+                        pos[i].append(((w + 1) * window * runs[i][2], sti["position"] + offset[i]))
+                    if 1.0 - sti["volume"] / nx >= 0.5:   # dF > 0 favours phi = 0
+                        g.shift_x(-1)
+                        offset[i] -= 1
+            b.close()
+            for i, (lam, dF, dt) in enumerate(runs):
+                t, x = np.array(pos[i]).T
+                v = np.polyfit(t, x, 1)[0]
+                vw = np.diff(x) / np.diff(t)
+                vth = -dF
+                res[f"lam{lam:g}"][f"{dF:g}"] = {
+                    "err_mean": float(abs(v / vth - 1.0)),
+                    "err_osc": float((vw.max() - vw.min()) / abs(vth)),
+                    "cells_travelled": float(abs(x[-1] - x[0])), "dt": dt}
+            for g in grids:
+                g.close()
+            out[name] = res
+    return out
+
+
 def shape_relaxation(dev):
     """Sec. 3.3: a cubic particle (half side 12) in 60^3, periodic, relaxed at
     constant volume by spfm_step_conserving for a fixed physical time (250),
@@ -503,6 +571,9 @@ def run_gpu(args):
     relax = None
     if rank == 0 and not args.no_relax:
         relax = shape_relaxation(dev)
+    friction = None
+    if rank == 0 and not args.no_friction:
+        friction = friction_1d(dev)
 
     # end to end through the public API from pinned host memory: upload the
     # initial field, E2E_STEPS steps, stats, read the field back
@@ -561,7 +632,7 @@ def run_gpu(args):
                          "avg_launch_ms": avg_kernel_ms,
                          "timed": "per step: stencil kernel + ghost-face kernel (events around 50-step chunks)"},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
-            "batched": batched, "serving": serving, "grain_sphericity": grain, "variants": variants, "bf16_storage": bf16, "shape_relaxation": relax,
+            "batched": batched, "serving": serving, "grain_sphericity": grain, "variants": variants, "bf16_storage": bf16, "shape_relaxation": relax, "friction_1d": friction,
             "last_stats": stats_seen[-1] if stats_seen else None,
             "stats_call": {"ms": (total_ms - step_ms) / max(1, len(stats_seen)), "every": STATS_EVERY,
                            "note": "interface stats between step chunks, host round trip included"},

@@ -59,7 +59,11 @@ typedef int spfm_status;
 
 enum { SPFM_F64 = 0, SPFM_F32 = 1, SPFM_BF16 = 2 };              /* storage type */
 enum { SPFM_PERIODIC = 0, SPFM_NOFLUX = 1, SPFM_CONTACT = 2 };   /* boundary kinds */
-enum { SPFM_TI_GLOBAL = 0, SPFM_TI_LOCAL = 1, SPFM_FD = 2 };     /* schemes */
+/* schemes: TI with one global direction, TI_n (local normal), and the CF
+ * (conventional finite-difference) models of Tab. 2 with the interpolation
+ * functions h3 = phi^2 (3 - 2 phi), h5 = phi^3 (10 - 15 phi + 6 phi^2) and
+ * h_Abel = phi^2 / (phi^2 + (1 - phi)^2) */
+enum { SPFM_TI_GLOBAL = 0, SPFM_TI_LOCAL = 1, SPFM_FD = 2, SPFM_FD_H5 = 3, SPFM_FD_HABEL = 4 };
 enum { SPFM_STATS_ENERGY = 1 };                                  /* stats flags */
 
 typedef struct spfm_grid spfm_grid;
@@ -144,7 +148,8 @@ spfm_status spfm_step(spfm_grid *g, int n_steps, double M, double Gamma, double 
  * alpha = sum_p (phi*_p - phi_p) / sum_p q(phi_p) (FP64 sums in a fixed order),
  * which is dF = alpha lambda Gamma / (4 M dt) in the driving term of Eq. 2.
  * Validation as spfm_step at dF = 0 (the phase-stability check of Sec. 3.1
- * cannot see a dF decided during the run).  Uses the grid's scratch.
+ * cannot see a dF decided during the run); schemes with h3 only (SPFM_EINVAL
+ * for SPFM_FD_H5 and SPFM_FD_HABEL).  Uses the grid's scratch.
  * dF_last (host pointer or NULL) receives the last step's dF; a non-NULL
  * dF_last synchronises the stream. */
 spfm_status spfm_step_conserving(spfm_grid *g, int n_steps, double M, double Gamma, double lambda,
@@ -181,6 +186,18 @@ spfm_status spfm_interface_stats_static(const spfm_grid_desc *desc, const void *
  * out[3] R_max, out[4] number of contour points, out[5..7] barycentre.  FP64,
  * uses the grid's scratch, synchronises the stream. */
 spfm_status spfm_sphericity(spfm_grid *g, int inside_phase, double *out8);
+
+/* Moving frame of the 1D friction study (Sec. 3.1: the system is moved back by
+ * one grid point whenever the favoured phase fills half of it): the current
+ * field shifted along x, phi_i <- phi_{i+cells}, the cells that open up taking
+ * the value of the row's end cell; written to the other buffer, which becomes
+ * current.  Ghosts are rebuilt when a model is known.  Asynchronous. */
+spfm_status spfm_shift_x(spfm_grid *g, int cells);
+/* The largest dt that spfm_step accepts for these parameters: 2 over the bound
+ * of the Euler Jacobian's spectral radius (the same validation, SPFM_EPHASE
+ * included).  No launch. */
+spfm_status spfm_max_dt(spfm_grid *g, double M, double Gamma, double lambda, double dx, double dF,
+                        int stencil, int scheme, double *dt_max);
 
 /* Copy the interior of the current field to/from a dense (nz, ny, nx) array of
  * the storage type; *_on_host selects a host or a device pointer.  set_field

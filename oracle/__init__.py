@@ -29,6 +29,7 @@ _lib = None
 
 PERIODIC, NOFLUX, CONTACT = 0, 1, 2
 TI_GLOBAL, TI_LOCAL, CF = 0, 1, 2
+CF_H5, CF_HABEL = 3, 4   # CF with the interpolation functions h5 and h_Abel (Tab. 2)
 
 
 def build(force: bool = False) -> str:
@@ -79,6 +80,7 @@ def _load():
             lib.oracle_step.argtypes = [P, dp, ctypes.c_int]
             lib.oracle_step.restype = ctypes.c_long
             lib.oracle_step_conserving.argtypes = [P, dp, ctypes.c_int, dp]
+            lib.oracle_shift_x.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
             lib.oracle_step_conserving.restype = ctypes.c_long
             lib.oracle_init_cube.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
                                              ctypes.c_double, ctypes.c_double, ctypes.c_double]
@@ -224,6 +226,15 @@ def step_conserving(p: Params, phi, n_steps: int):
     pc = p.c()
     lib.oracle_step_conserving(ctypes.byref(pc), _dp(a), int(n_steps), _dp(dF))
     return a, dF[:int(n_steps)]
+
+
+def shift_x(p: Params, phi, cells: int) -> np.ndarray:
+    """The moving frame of the 1D friction study: phi_i <- phi_{i+cells}, the
+    vacated cells taking the value of the row's end cell."""
+    lib = _load()
+    a = _field(p, phi).copy()
+    lib.oracle_shift_x(_dp(a), p.nx, p.ny, p.nz, int(cells))
+    return a
 
 
 def step(p: Params, phi, n_steps: int) -> np.ndarray:

@@ -27,7 +27,8 @@
  *   - default ponderations gamma = (1,0,0), (1/3,2/3,0), (1/2,1/3,1/6) for 6, 18,
  *     26 neighbours (fourth-order isotropy of the discrete Laplacian), and
  *     C_Gamma = 2/3 (interface energy Gamma in the continuum limit);
- *   - forward Euler in time; the driving term uses h3 = phi^2 (3 - 2 phi);
+ *   - forward Euler in time; the driving term uses h3 = phi^2 (3 - 2 phi),
+ *     or, for the CF variants of Tab. 2, h5 or h_Abel;
  *   - NOFLUX ghost = copy of the adjacent interior cell; CONTACT ghost by
  *     Eq. 7 with the signed a = tanh(2 (x_ghost - x_source).n / lambda);
  *   - TI_n: n = grad psi / |grad psi| with psi = (lambda/2) artanh(1 - 2 phi),
@@ -131,6 +132,23 @@ void oracle_init_cube(double *phi, int nx, int ny, int nz, const double ctr[3], 
             }
 }
 
+void oracle_shift_x(double *phi, int nx, int ny, int nz, int cells)
+{
+    double *row = (double *)malloc(sizeof(double) * (size_t)nx);
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j) {
+            double *r = phi + ((size_t)k * ny + j) * nx;
+            for (int i = 0; i < nx; ++i) {
+                int src = i + cells;
+                if (src < 0) src = 0;
+                if (src > nx - 1) src = nx - 1;
+                row[i] = r[src];
+            }
+            memcpy(r, row, sizeof(double) * (size_t)nx);
+        }
+    free(row);
+}
+
 /* ---------------------------------------------------------------- ghosts */
 
 #define PADX(p) ((p)->nx + 2)
@@ -195,6 +213,33 @@ void oracle_fill_ghosts(const orc_params *p, const double *phi, double *pad)
 static double h3_prime(double phi)
 {
     return 6.0 * phi * (1.0 - phi);
+}
+
+/* Tab. 2: h5 = phi^3 (10 - 15 phi + 6 phi^2) and
+ * h_Abel = phi^2 / (phi^2 + (1 - phi)^2), differentiated by hand */
+static double h5_prime(double phi)
+{
+    return 30.0 * phi * phi * (1.0 - phi) * (1.0 - phi);
+}
+
+static double habel_prime(double phi)
+{
+    const double d = phi * phi + (1.0 - phi) * (1.0 - phi);
+    return 2.0 * phi * (1.0 - phi) / (d * d);
+}
+
+/* the interpolation function of the scheme: h5 and h_Abel belong to CF models
+ * only (Tab. 2); every other scheme uses h3 */
+static double h_prime(const orc_params *p, double phi)
+{
+    if (p->scheme == ORC_CF_H5) return h5_prime(phi);
+    if (p->scheme == ORC_CF_HABEL) return habel_prime(phi);
+    return h3_prime(phi);
+}
+
+static int is_cf(const orc_params *p)
+{
+    return p->scheme == ORC_CF || p->scheme == ORC_CF_H5 || p->scheme == ORC_CF_HABEL;
 }
 
 /* derivative of the TI potential of Eq. 6 w.r.t. phi, multiplied out:
@@ -284,7 +329,7 @@ long oracle_rhs(const orc_params *p, const double *phi, double *R)
                 size_t c = PIDX(p, i, j, k);
                 double ph = pad[c];
                 const double *a = a_glob;
-                int use_cf = (p->scheme == ORC_CF);
+                int use_cf = is_cf(p);
                 if (p->scheme == ORC_TI_LOCAL) {
                     use_cf = local_coupling(p, pad, c, a_loc);
                     a = a_loc;
@@ -299,7 +344,7 @@ long oracle_rhs(const orc_params *p, const double *phi, double *R)
                     double gp = use_cf ? g_cf_prime(ph) : g_ti_prime(ph, a[kk], lam * lam / r2, &bad);
                     dFdphi_int += w[kk] * (gp - lam * lam / r2 * lap);
                 }
-                double dFdphi = pref_int * dFdphi_int + p->dF * h3_prime(ph);
+                double dFdphi = pref_int * dFdphi_int + p->dF * h_prime(p, ph);
                 R[((size_t)k * ny + j) * nx + i] = -pref * dFdphi;
                 nbad += bad;
             }
@@ -335,11 +380,11 @@ long oracle_step_conserving(const orc_params *p, double *phi, int n_steps, doubl
         double sum_r = 0.0, sum_h = 0.0;
         for (size_t c = 0; c < n; ++c) {
             sum_r += R[c];
-            sum_h += h3_prime(phi[c]);
+            sum_h += h_prime(p, phi[c]);
         }
         /* the homogeneous dF for which sum_p (R_p - pref dF h3'(phi_p)) = 0 */
         const double dF = sum_h != 0.0 ? sum_r / (pref * sum_h) : 0.0;
-        for (size_t c = 0; c < n; ++c) phi[c] += p->dt * (R[c] - pref * dF * h3_prime(phi[c]));
+        for (size_t c = 0; c < n; ++c) phi[c] += p->dt * (R[c] - pref * dF * h_prime(p, phi[c]));
         if (dF_out) dF_out[s] = dF;
     }
     free(R);
@@ -402,7 +447,7 @@ double oracle_energy(const orc_params *p, const double *phi)
                 double ph = pad[c];
                 const double *a = a_glob;
                 double a_loc[13];
-                int use_cf = (p->scheme == ORC_CF);
+                int use_cf = is_cf(p);
                 if (p->scheme == ORC_TI_LOCAL) {
                     use_cf = local_coupling(p, pad, c, a_loc);
                     a = a_loc;

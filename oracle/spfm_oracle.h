@@ -39,7 +39,15 @@ extern "C" {
 enum { ORC_PERIODIC = 0, ORC_NOFLUX = 1, ORC_CONTACT = 2 };
 /* schemes: TI with one global coupling direction, TI with the local normal,
  * conventional continuum-field finite differences (CF + h3) */
-enum { ORC_TI_GLOBAL = 0, ORC_TI_LOCAL = 1, ORC_CF = 2 };
+enum { ORC_TI_GLOBAL = 0, ORC_TI_LOCAL = 1, ORC_CF = 2,
+       /* CF with the interpolation functions h5 and h_Abel of Tab. 2 */
+       ORC_CF_H5 = 3, ORC_CF_HABEL = 4 };
+
+/* Shift the field along x by `cells` (phi_i <- phi_{i+cells}), filling the
+ * vacated cells with the value of the row's last (first) cell: the moving
+ * frame of the 1D friction study (Sec. 3.1), which moves the system back by
+ * one grid point whenever the favoured phase fills half of it. */
+void oracle_shift_x(double *phi, int nx, int ny, int nz, int cells);
 
 typedef struct {
     int nx, ny, nz;

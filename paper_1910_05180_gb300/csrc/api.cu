@@ -66,8 +66,9 @@ int build_model(spfm_grid *g, double M, double Gamma, double lambda, double dx, 
         return fail(g, SPFM_EINVAL, "spfm_step: M, Gamma, lambda, dx, dt must be finite and > 0");
     if (stencil != 6 && stencil != 18 && stencil != 26)
         return fail(g, SPFM_EINVAL, "spfm_step: stencil %d not in {6, 18, 26}", stencil);
-    if (scheme != SPFM_TI_GLOBAL && scheme != SPFM_TI_LOCAL && scheme != SPFM_FD)
+    if (scheme != SPFM_TI_GLOBAL && scheme != SPFM_TI_LOCAL && !is_fd_scheme(scheme))
         return fail(g, SPFM_EINVAL, "spfm_step: unknown scheme %d", scheme);
+    m.interp = scheme == SPFM_FD_H5 ? 1 : (scheme == SPFM_FD_HABEL ? 2 : 0);
     const int nd = n_dirs(stencil);
     default_gamma(stencil, g->d.gamma, m.gamma);
     const double nu[3] = {1.0, 0.5, 0.75};   // 3 / m_j, m = (3, 6, 4) directions per shell
@@ -123,7 +124,7 @@ int build_model(spfm_grid *g, double M, double Gamma, double lambda, double dx, 
         lap = std::max(lap, s);
     }
     double pot = 0.0;
-    if (scheme == SPFM_FD) {
+    if (is_fd_scheme(scheme)) {
         pot = m.kappa;
     } else {
         for (int k = 0; k < nd; ++k) {
@@ -136,18 +137,22 @@ int build_model(spfm_grid *g, double M, double Gamma, double lambda, double dx, 
             pot += 4.0 * m.ck[k] * A / (1.0 - A);
         }
     }
-    m.bound = lap + pot + fabs(m.kmu);
+    // the driving term's derivative: kmu (d/dphi q)          <= kmu     (h3),
+    // 5 kmu (d/dphi q^2) <= 2.5 kmu (h5), kmu/3 (d/dphi q/(1-2q)^2) <= kmu (h_Abel)
+    m.bound = lap + pot + (m.interp == 1 ? 2.5 : 1.0) * fabs(m.kmu);
     if (dt * m.bound > 2.0)
         return fail(g, SPFM_EUNSTABLE,
                     "spfm_step: dt = %g exceeds the explicit-Euler bound 2/%g = %g", dt, m.bound,
                     2.0 / m.bound);
-    if (scheme == SPFM_FD) {
+    // phase stability (Sec. 3.1): a barrier between the phases.  h3: |dF~| <
+    // 8/(3 C lambda~); h_Abel: |dF~| < 8/(C lambda~) (derived; the paper prints
+    // 440/(3 C lambda~)); h5: at any dF.
+    if (scheme == SPFM_FD || scheme == SPFM_FD_HABEL) {
         const double lam_t = lambda / dx, dF_t = fabs(dF) * dx / Gamma;
-        const double limit = 8.0 / (3.0 * m.Cg * lam_t);
+        const double limit = (scheme == SPFM_FD ? 8.0 / 3.0 : 8.0) / (m.Cg * lam_t);
         if (dF_t >= limit)
             return fail(g, SPFM_EPHASE,
-                        "spfm_step: CF driving force |dF dx/Gamma| = %g is beyond phase stability "
-                        "8/(3 C_Gamma lambda/dx) = %g",
+                        "spfm_step: CF driving force |dF dx/Gamma| = %g is beyond phase stability %g",
                         dF_t, limit);
     }
     return SPFM_OK;
@@ -425,6 +430,8 @@ spfm_status spfm_step_conserving(spfm_grid *g, int n_steps, double M, double Gam
 {
     if (!g) return fail(nullptr, SPFM_EINVAL, "spfm_step_conserving: grid is NULL");
     if (n_steps < 0) return fail(g, SPFM_EINVAL, "spfm_step_conserving: n_steps < 0");
+    if (scheme == SPFM_FD_H5 || scheme == SPFM_FD_HABEL)
+        return fail(g, SPFM_EINVAL, "spfm_step_conserving: the volume correction uses h3 (TI, TI_n or CF + h3)");
     Model m;
     spfm_status st = build_model(g, M, Gamma, lambda, dx, dt, 0.0, stencil, scheme, m);
     if (st != SPFM_OK) return st;
@@ -545,6 +552,30 @@ spfm_status spfm_get_field(spfm_grid *g, void *dst, int dst_on_host)
 {
     if (!g || !dst) return fail(g, SPFM_EINVAL, "spfm_get_field: NULL argument");
     return copy_field(g, dst, dst_on_host, 0);
+}
+
+spfm_status spfm_shift_x(spfm_grid *g, int cells)
+{
+    if (!g) return fail(nullptr, SPFM_EINVAL, "spfm_shift_x: grid is NULL");
+    if (cells == 0) return SPFM_OK;
+    cudaError_t e = launch_shift_x(g->geom, g->d.dtype, g->d.field[g->cur], g->d.field[1 - g->cur], cells,
+                                   stream_of(g));
+    if (e != cudaSuccess) return cuda_fail(g, e, "spfm_shift_x");
+    g->cur ^= 1;
+    g->ghosts_dirty = true;
+    if (g->lambda > 0.0) return refresh_ghosts(g, g->lambda, g->dx);
+    return SPFM_OK;
+}
+
+spfm_status spfm_max_dt(spfm_grid *g, double M, double Gamma, double lambda, double dx, double dF, int stencil,
+                        int scheme, double *dt_max)
+{
+    if (!g || !dt_max) return fail(g, SPFM_EINVAL, "spfm_max_dt: NULL argument");
+    Model m;
+    const spfm_status st = build_model(g, M, Gamma, lambda, dx, 1e-300, dF, stencil, scheme, m);
+    if (st != SPFM_OK) return st;
+    *dt_max = 2.0 / m.bound;
+    return SPFM_OK;
 }
 
 spfm_status spfm_set_field(spfm_grid *g, const void *src, int src_on_host)

@@ -266,7 +266,7 @@ spfm_status spfm_batch_step(spfm_batch *b, int n_steps, const spfm_step_args *ar
         gj.cur = g->cur;
     }
     if (n_steps == 0) return SPFM_OK;
-    const int kind = scheme == SPFM_FD ? 0 : 5;
+    const int kind = is_fd_scheme(scheme) ? 0 : 5;
     e = cudaMemcpyAsync(b->scratch + b->L.grids, b->h_grids.data(), rec * b->n, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->scratch + b->L.ghosts, b->h_ghosts.data(), sizeof(GhostJob) * b->n,

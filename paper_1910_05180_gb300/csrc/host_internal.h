@@ -38,6 +38,7 @@ struct Model {
     int nterms;
     double beta[spfm::kMaxTerms], A[spfm::kMaxTerms];
     double kmu, kappa, D, Cg;
+    int interp;     // CF driving term: 0 h3, 1 h5, 2 h_Abel
     double aface[6];
     double bound;   // upper bound of the spectral radius of the Euler Jacobian
 };
@@ -81,6 +82,7 @@ void fill_coef(const spfm_grid *g, const Model &m, double dt, int stencil, spfm:
     c.ctdt = (T)(ct * dt);
     c.nkmudt = (T)(-m.kmu * dt);
     c.nkapdt = (T)(-m.kappa * dt);
+    c.interp = m.interp;
 }
 
 // TI_n constants of the step kernels: lambda/2, 1/(2 dx), 2 dx/lambda and the

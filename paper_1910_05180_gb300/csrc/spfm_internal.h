@@ -77,7 +77,15 @@ struct StepCoef {
     // TI_n (local normal): per-direction c_k, (lambda/2), 1/(2 dx), 2 dx/lambda, clamp
     T ck[kMaxTerms];
     T half_lam, inv_2dx, two_dx_over_lam, eps;
+    // CF models: interpolation function of the driving term, 0 h3, 1 h5, 2 h_Abel
+    int interp;
 };
+
+// the CF models of Tab. 2 (any interpolation function)
+__host__ __device__ inline bool is_fd_scheme(int scheme)
+{
+    return scheme == SPFM_FD || scheme == SPFM_FD_H5 || scheme == SPFM_FD_HABEL;
+}
 
 // Ghost mapping for one axis: at most one cell outside [0, n).  Returns the
 // source coordinate and sets *contact when a contact-angle transform applies.
@@ -156,6 +164,9 @@ cudaError_t launch_init(const InitArgs &a, void *field, cudaStream_t st);
 // 2 * kStatsBlocks doubles, alpha_out (device) receives alpha.
 cudaError_t launch_conserve(const GridGeom &g, int dtype, const void *src, void *dst, double *partials,
                             double *alpha_out, cudaStream_t st);
+
+// Interior of dst = interior of src shifted along x by cells (frame.cu).
+cudaError_t launch_shift_x(const GridGeom &g, int dtype, const void *src, void *dst, int cells, cudaStream_t st);
 
 // Ghost layer of a buffer from its interior: all faces (x_faces = 1) or the y
 // and z faces only.  Face sizes must stay below 2^31 cells.

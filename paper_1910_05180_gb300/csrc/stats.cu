@@ -413,7 +413,7 @@ __device__ __forceinline__ void stats_pass(const StatsArgs &a, const S *f, doubl
                     const double nb = rd<S>(f, cell_index(a.g, i + d.x, j + d.y, k + d.z));
                     const double dp = nb - ph;
                     e += a.w[kk] * (0.5 * a.lambda * a.lambda * dp * dp / r2 +
-                                    potential(ph, a.a[kk], a.lambda * a.lambda / r2, a.scheme == SPFM_FD));
+                                    potential(ph, a.a[kk], a.lambda * a.lambda / r2, is_fd_scheme(a.scheme)));
                 }
                 v[7] += e_pref * e;
             }

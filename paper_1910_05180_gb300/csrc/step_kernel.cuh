@@ -657,7 +657,16 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
                         const P q1 = K::mul(ph, K::sub(PC.one, ph));          // q = phi (1 - phi)
                         P w;   // -dt (potential / q + 4 M dF / (lambda Gamma))
                         if (KIND == 0) {
-                            w = K::fma(sg, PC.nkap, PC.nkmu);
+                            // driving term -dt pref dF h'(phi) = q (nkmu f): f = 1 for h3,
+                            // 5 q for h5, 1/(3 (1 - 2q)^2) for h_Abel
+                            P drive = PC.nkmu;
+                            if (C.interp == 1) {
+                                drive = K::mul(PC.nkmu, K::mul(K::mk(T(5), T(5)), q1));
+                            } else if (C.interp == 2) {
+                                const P d = K::fma(K::mk(T(-2), T(-2)), q1, PC.one);
+                                drive = K::div(PC.nkmu, K::mul(K::mk(T(3), T(3)), K::mul(d, d)));
+                            }
+                            w = K::fma(sg, PC.nkap, drive);
                         } else if (KIND == 6) {
                             const P s2 = K::mk(C.inv_2dx, C.inv_2dx);
                             const P gz = K::mul(K::sub(p[r].psi[q], m[r].psi[q]), s2);
@@ -842,7 +851,7 @@ cudaError_t launch_step_t(const StepCoef<T> &c, const S *src, S *dst, int *err, 
     const dim3 grid(gxn, gyn, (c.g.nz + zchunk - 1) / zchunk);
     // exact group counts 1..4 get their own kernels; 0 groups (all A_k = 0)
     // runs the one-group kernel with beta = 0
-    const int kind = cfg.scheme == SPFM_FD ? 0
+    const int kind = is_fd_scheme(cfg.scheme) ? 0
                      : cfg.scheme == SPFM_TI_LOCAL ? 6
                                                    : (c.nterms <= 4 ? (c.nterms < 1 ? 1 : c.nterms) : 5);
     const PackCoef<T> pc = make_pack_coef<T>(c);

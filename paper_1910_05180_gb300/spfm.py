@@ -26,6 +26,7 @@ SPFM_ECUDA, SPFM_ENONFINITE, SPFM_ETIMEOUT, SPFM_ENOMEM = -4, -5, -6, -7
 SPFM_F64, SPFM_F32, SPFM_BF16 = 0, 1, 2
 SPFM_PERIODIC, SPFM_NOFLUX, SPFM_CONTACT = 0, 1, 2
 SPFM_TI_GLOBAL, SPFM_TI_LOCAL, SPFM_FD = 0, 1, 2
+SPFM_FD_H5, SPFM_FD_HABEL = 3, 4   # CF with the interpolation functions h5 and h_Abel (Tab. 2)
 SPFM_STATS_ENERGY = 1
 
 TORCH_DTYPE = {SPFM_F64: torch.float64, SPFM_F32: torch.float32, SPFM_BF16: torch.bfloat16}
@@ -89,6 +90,8 @@ SIGNATURES = [
     ("spfm_init_cube", _I, [_P, ctypes.POINTER(_D), _D, _D, _D]),
     ("spfm_step", _I, [_P, _I, _D, _D, _D, _D, _D, _D, _I, _I]),
     ("spfm_step_conserving", _I, [_P, _I, _D, _D, _D, _D, _D, _I, _I, ctypes.POINTER(_D)]),
+    ("spfm_shift_x", _I, [_P, _I]),
+    ("spfm_max_dt", _I, [_P, _D, _D, _D, _D, _D, _I, _I, ctypes.POINTER(_D)]),
     ("spfm_interface_stats", _I, [_P, _I, ctypes.POINTER(Stats)]),
     ("spfm_interface_stats_static", _I, [ctypes.POINTER(GridDesc), _P, _D, _D, ctypes.POINTER(Stats)]),
     ("spfm_sphericity", _I, [_P, _I, ctypes.POINTER(_D)]),
@@ -170,6 +173,16 @@ def spfm_init_cube(h, ctr, half, lam, dx):
 
 def spfm_step(h, n_steps, M, Gamma, lam, dx, dt, dF, stencil, scheme):
     _check(load().spfm_step(h, int(n_steps), M, Gamma, lam, dx, dt, dF, int(stencil), int(scheme)), h)
+
+
+def spfm_shift_x(h, cells):
+    _check(load().spfm_shift_x(h, int(cells)), h)
+
+
+def spfm_max_dt(h, M, Gamma, lam, dx, dF, stencil, scheme):
+    out = ctypes.c_double(0.0)
+    _check(load().spfm_max_dt(h, M, Gamma, lam, dx, dF, int(stencil), int(scheme), ctypes.byref(out)), h)
+    return out.value
 
 
 def spfm_step_conserving(h, n_steps, M, Gamma, lam, dx, dt, stencil, scheme):
@@ -277,6 +290,13 @@ class Grid:
     def step(self, n_steps, M=1.0, Gamma=1.0, lam=4.0, dx=1.0, dt=0.1, dF=0.0, stencil=26,
              scheme=SPFM_TI_GLOBAL):
         spfm_step(self.handle, n_steps, M, Gamma, lam, dx, dt, dF, stencil, scheme)
+
+    def shift_x(self, cells):
+        """Moving frame: phi_i <- phi_{i+cells} (end cells repeated)."""
+        spfm_shift_x(self.handle, cells)
+
+    def max_dt(self, M=1.0, Gamma=1.0, lam=4.0, dx=1.0, dF=0.0, stencil=26, scheme=SPFM_TI_GLOBAL):
+        return spfm_max_dt(self.handle, M, Gamma, lam, dx, dF, stencil, scheme)
 
     def step_conserving(self, n_steps, M=1.0, Gamma=1.0, lam=4.0, dx=1.0, dt=0.1, stencil=26,
                         scheme=SPFM_TI_GLOBAL):

@@ -158,3 +158,32 @@ def test_last_error_is_thread_local_without_grid(lib):
     with pytest.raises(S.SpfmError):
         S.spfm_layout(_desc(dtype=9))
     assert "dtype" in S.spfm_last_error(None)
+
+
+def test_phase_stability_of_the_other_cf_models(lib):
+    """Tab. 2 CF variants: h_Abel keeps a barrier below |dF~| = 8/(C_Gamma lambda~)
+    (the barrier criterion of Sec. 3.1 applied to h_Abel; reading r20), h5 at
+    any dF; spfm_max_dt answers the same validation without a launch."""
+    h = _fake_grid(lib)
+    try:
+        lam, Cg = 4.0, 2.0 / 3.0
+        limit = 8.0 / (Cg * lam)
+        with pytest.raises(S.SpfmError) as e:
+            S.spfm_step(h, 0, 1.0, 1.0, lam, 1.0, 0.001, 1.001 * limit, 26, S.SPFM_FD_HABEL)
+        assert e.value.status == S.SPFM_EPHASE
+        S.spfm_step(h, 0, 1.0, 1.0, lam, 1.0, 0.001, 0.999 * limit, 26, S.SPFM_FD_HABEL)
+        S.spfm_step(h, 0, 1.0, 1.0, lam, 1.0, 0.001, 50 * limit, 26, S.SPFM_FD_H5)
+        with pytest.raises(S.SpfmError) as e:
+            S.spfm_max_dt(h, 1.0, 1.0, lam, 1.0, 1.001 * limit, 26, S.SPFM_FD_HABEL)
+        assert e.value.status == S.SPFM_EPHASE
+        for scheme in (S.SPFM_FD, S.SPFM_FD_H5, S.SPFM_FD_HABEL, S.SPFM_TI_GLOBAL, S.SPFM_TI_LOCAL):
+            dt = S.spfm_max_dt(h, 1.0, 1.0, lam, 1.0, 0.01, 26, scheme)
+            S.spfm_step(h, 0, 1.0, 1.0, lam, 1.0, 0.999 * dt, 0.01, 26, scheme)
+            with pytest.raises(S.SpfmError) as e:
+                S.spfm_step(h, 0, 1.0, 1.0, lam, 1.0, 1.001 * dt, 0.01, 26, scheme)
+            assert e.value.status == S.SPFM_EUNSTABLE
+        with pytest.raises(S.SpfmError) as e:
+            S.spfm_step_conserving(h, 0, 1.0, 1.0, lam, 1.0, 0.01, 26, S.SPFM_FD_H5)
+        assert e.value.status == S.SPFM_EINVAL
+    finally:
+        S.spfm_destroy_grid(h)

@@ -1,0 +1,83 @@
+"""The CF variants of Tab. 2 (interpolation functions h5 and h_Abel) and the
+moving frame of the 1D friction study (Sec. 3.1), on the GPU against the
+oracle.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1910_05180_gb300 import spfm as S
+from paper_1910_05180_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+TOL = {S.SPFM_F64: 1e-12, S.SPFM_F32: 2e-5}
+OSCHEME = {S.SPFM_FD_H5: O.CF_H5, S.SPFM_FD_HABEL: O.CF_HABEL}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    S.load()
+
+
+def _upload(g, phi, dtype):
+    t = torch.from_numpy(phi).to(S.TORCH_DTYPE[dtype])
+    g.set_field(t.cuda())
+    return t.double().numpy()
+
+
+@pytest.mark.parametrize("dtype", [S.SPFM_F64, S.SPFM_F32])
+@pytest.mark.parametrize("scheme", [S.SPFM_FD_H5, S.SPFM_FD_HABEL])
+def test_cf_variant_steps_match_oracle(dtype, scheme):
+    n = WL.random_normal(np.random.default_rng(61))
+    shape = (37, 21, 19)
+    lam, dt, dF = 2.5, 0.04, 0.08
+    g = S.Grid(*shape, dtype=dtype, bc=(S.SPFM_CONTACT,) * 6, n=n)
+    p = O.Params(*shape, bc=(O.CONTACT,) * 6, n=tuple(n), lam=lam, dt=dt, dF=dF, stencil=26,
+                 scheme=OSCHEME[scheme])
+    rng = np.random.default_rng(62)
+    phi0 = O.init_planar(p, float(n @ (np.array(shape) - 1) / 2.0)) + 0.003 * rng.random(p.shape)
+    start = _upload(g, phi0, dtype)
+    g.step(30, lam=lam, dt=dt, dF=dF, stencil=26, scheme=scheme)
+    ref = O.step(p, start, 30)
+    assert np.abs(g.get_field(to_host=True).double().numpy() - ref).max() <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [S.SPFM_F64, S.SPFM_F32])
+def test_moving_frame_shift_matches_oracle(dtype):
+    shape = (45, 6, 5)
+    g = S.Grid(*shape, dtype=dtype, bc=(S.SPFM_NOFLUX, S.SPFM_NOFLUX) + (S.SPFM_PERIODIC,) * 4)
+    p = O.Params(*shape)
+    start = _upload(g, np.random.default_rng(63).random(p.shape), dtype)
+    want = start
+    for cells in (1, -3, 7, -1):
+        g.shift_x(cells)
+        want = O.shift_x(p, want, cells)
+        assert np.array_equal(g.get_field(to_host=True).double().numpy(), want)
+
+
+def test_1d_frame_keeps_the_interface_and_its_velocity():
+    """A planar interface on 64 x 1 x 1 driven by dF (TI + h3, 27-point): moving
+    the frame by one cell whenever the favoured phase fills half the system
+    keeps the interface near the middle, and the position measured in the
+    fixed frame (shifts added back) advances at v_th = -M dF/Gamma."""
+    lam, dF, dt = 3.0, 0.05, 0.05
+    bc = (S.SPFM_NOFLUX, S.SPFM_NOFLUX) + (S.SPFM_PERIODIC,) * 4
+    g = S.Grid(64, 1, 1, dtype=S.SPFM_F64, bc=bc, n=(1.0, 0.0, 0.0))
+    g.init_planar(31.5, lam)
+    offset, xs, ts = 0, [], []
+    for window in range(80):
+        g.step(100, lam=lam, dt=dt, dF=dF, stencil=26)
+        st = g.stats()
+        if window >= 20:
+            xs.append(st["position"] + offset)   # fixed-frame position: each move added one cell
+            ts.append((window + 1) * 100 * dt)
+        if 1.0 - st["volume"] / 64.0 >= 0.5:   # dF > 0 favours phi = 0
+            g.shift_x(-1)
+            offset -= 1
+    assert offset <= -8                        # the frame moved: the interface travelled cells
+    v = np.polyfit(ts, xs, 1)[0]
+    assert abs(v / (-dF) - 1.0) < 1e-3

@@ -167,9 +167,18 @@ def test_exact_translation_velocity(stencil):
 # ------------------------------------------------- brute force: autograd of Eq. 1
 
 
-def _energy_torch(phi, w, d, shell, lam, dx, Gamma, Cg, dF, a=None):
+def _h_torch(phi, interp):
+    """The interpolation functions of Tab. 2, typed from the table."""
+    if interp == "h5":
+        return phi ** 3 * (10 - 15 * phi + 6 * phi ** 2)
+    if interp == "abel":
+        return phi ** 2 / (phi ** 2 + (1 - phi) ** 2)
+    return phi ** 2 * (3 - 2 * phi)
+
+
+def _energy_torch(phi, w, d, shell, lam, dx, Gamma, Cg, dF, a=None, interp="h3"):
     """Eq. 1 typed from the paper (periodic forward differences), with Eq. 6 or
-    the CF potential; F = sum_p f_p dx^3."""
+    the CF potential and the interpolation function of Tab. 2; F = sum_p f_p dx^3."""
     q = phi * (1 - phi)
     s = 1 - 2 * phi
     f = torch.zeros_like(phi)
@@ -188,13 +197,12 @@ def _energy_torch(phi, w, d, shell, lam, dx, Gamma, Cg, dF, a=None):
             else:
                 g = lam ** 2 / r ** 2 * (q + (1 - A) / (4 * A) * torch.log((1 - A) / (1 - A * s ** 2)))
         f = f + w[k] * (lam ** 2 / 2 * dplus ** 2 + g)
-    h3 = phi ** 2 * (3 - 2 * phi)
-    f = Gamma / (Cg * lam) * f + dF * h3
+    f = Gamma / (Cg * lam) * f + dF * _h_torch(phi, interp)
     return f.sum() * dx ** 3
 
 
 @pytest.mark.parametrize("stencil", [6, 18, 26])
-@pytest.mark.parametrize("scheme", [O.TI_GLOBAL, O.CF])
+@pytest.mark.parametrize("scheme", [O.TI_GLOBAL, O.CF, O.CF_H5, O.CF_HABEL])
 def test_rhs_is_energy_gradient_4cubed(stencil, scheme):
     """Eq. 2: 3 lambda Gamma dphi/dt = -2 M dF/dphi.  Autograd of Eq. 1 on a
     periodic 4^3 random field reproduces the oracle's right-hand side."""
@@ -208,16 +216,17 @@ def test_rhs_is_energy_gradient_4cubed(stencil, scheme):
     assert nbad == 0
     w, _ = O.weights(p)
     d, shell = O.directions()
-    a = None if scheme == O.CF else np.tanh(2 * dx * (d @ n) / lam)
+    a = None if scheme in (O.CF, O.CF_H5, O.CF_HABEL) else np.tanh(2 * dx * (d @ n) / lam)
+    interp = {O.CF_H5: "h5", O.CF_HABEL: "abel"}.get(scheme, "h3")
     t = torch.tensor(phi, dtype=torch.float64, requires_grad=True)
-    F = _energy_torch(t, w, d, shell, lam, dx, G, Cg, dF, a)
+    F = _energy_torch(t, w, d, shell, lam, dx, G, Cg, dF, a, interp)
     (grad,) = torch.autograd.grad(F, t)
     dFdphi = grad.numpy() / dx ** 3
     R_ref = -2 * M / (3 * lam * G) * dFdphi
     assert np.abs(R - R_ref).max() < 1e-12 * max(1.0, np.abs(R_ref).max())
     # the oracle's own energy equals Eq. 1 typed here (dF = 0 part)
     p0 = O.Params(**{**p.__dict__, "dF": 0.0})
-    F0 = _energy_torch(t.detach(), w, d, shell, lam, dx, G, Cg, 0.0, a).item()
+    F0 = _energy_torch(t.detach(), w, d, shell, lam, dx, G, Cg, 0.0, a, interp).item()
     assert abs(O.energy(p0, phi) - F0) < 1e-12 * abs(F0)
 
 
@@ -278,6 +287,37 @@ def test_phase_stability_bound_cf():
         vals = np.array([O.rhs(p, np.full((1, 1, 1), x))[0][0, 0, 0] for x in phis])
         has_zero = bool(np.any(np.sign(vals[1:]) != np.sign(vals[:-1])))
         assert has_zero == expect
+
+
+@pytest.mark.parametrize("scheme,bound", [(O.CF_HABEL, 8.0), (O.CF_H5, None)])
+def test_phase_stability_of_the_other_interpolations(scheme, bound):
+    """The barrier criterion of Sec. 3.1 for the Tab. 2 interpolations, from
+    the uniform-field RHS (brute force over phi).  h5: a barrier at any dF
+    (h5' vanishes to second order at both phases).  h_Abel: h' = 8 q / (1 + s^2)^2,
+    so df/dphi = q (16 s / (C lambda~) + 8 dF~ / (1 + s^2)^2) (Gamma, dx units)
+    changes sign inside (0, 1) iff |dF~| < 8 / (C_Gamma lambda~) (reading r20:
+    the paper prints 440 / (3 C_Gamma lambda~))."""
+    lam, dx, Cg = 3.0, 1.0, 2.0 / 3.0
+    phis = np.linspace(1e-4, 1 - 1e-4, 4001)
+    cases = ((0.97, True), (1.03, False)) if bound else ((1.0, True), (30.0, True), (300.0, True))
+    for frac, expect in cases:
+        dF = frac * (bound / (Cg * lam / dx) if bound else 8.0 / (3 * Cg * lam / dx))
+        p = O.Params(1, 1, 1, lam=lam, dx=dx, C_gamma=Cg, dF=dF, scheme=scheme, stencil=26)
+        vals = np.array([O.rhs(p, np.full((1, 1, 1), x))[0][0, 0, 0] for x in phis])
+        has_zero = bool(np.any(np.sign(vals[1:]) != np.sign(vals[:-1])))
+        assert has_zero == expect, (frac, dF)
+
+
+def test_moving_frame_shift():
+    """The 1D study's moving frame: phi_i <- phi_{i+1} with the end cell
+    repeated; on the ideal profile a shift by one cell equals the profile
+    moved by -dx (away from the last cell)."""
+    p = O.Params(40, 2, 3, lam=3.0)
+    phi = O.init_planar(p, 20.3)
+    got = O.shift_x(p, phi, 1)
+    assert np.abs(got[..., :-1] - O.init_planar(p, 19.3)[..., :-1]).max() < 1e-15
+    assert np.all(got[..., -1] == phi[..., -1])
+    assert np.all(O.shift_x(p, phi, -2)[..., :2] == phi[..., :1])
 
 
 # ---------------------------------------------------------------- energy
