@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-storage leg")
     ap.add_argument("--no-relax", action="store_true", help="skip the constant-volume shape relaxation")
     ap.add_argument("--no-friction", action="store_true", help="skip the 1D friction study")
+    ap.add_argument("--no-force-scan", action="store_true", help="skip the force-oscillation scan")
     ap.add_argument("--n", type=int, default=512, help="grid edge")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -373,6 +374,57 @@ def friction_1d(dev, steps: int = 24000, window: int = 200):
     return out
 
 
+def orientation_paths():
+    """The two rotation paths of the force-oscillation scan: about [001] from
+    [100] to [110], and from [100] towards [011] up to [111] (reading r22)."""
+    out = []
+    # 0..45 degrees plus the [210] normal itself (atan(1/2) = 26.57 degrees), a <120> member
+    for deg in sorted(list(np.linspace(0.0, 45.0, 10)) + [float(np.degrees(np.arctan(0.5)))]):
+        t = np.radians(deg)
+        out.append(("001", float(deg), (float(np.cos(t)), float(np.sin(t)), 0.0)))
+    for deg in np.linspace(0.0, np.degrees(np.arctan(np.sqrt(2.0))), 10):
+        t = np.radians(deg)
+        out.append(("011", float(deg), (float(np.cos(t)), float(np.sin(t) / np.sqrt(2.0)),
+                                        float(np.sin(t) / np.sqrt(2.0)))))
+    return out
+
+
+def force_scan_sum(S, n, lam, scheme, shift, u=(0.0, 0.0, 0.0), nx=300):
+    """Sum over a 300 x 1 x 1 line of the discrete equilibrium expression E_p of
+    Eq. 4 for the ideal profile (Eq. 3) with normal n through x = nx/2 + shift
+    (contact faces, Eq. 7, supply the exact profile as every neighbour).  One
+    FP64 step at dF = 0 gives R_p = (2M/(3 C_Gamma lambda^2)) E_p; here
+    M = 1, C_Gamma = 2/3, so E_p = lambda^2 R_p.  u: the TI_<hkl> coupling
+    direction (zero: n)."""
+    g = S.Grid(nx, 1, 1, dtype=S.SPFM_F64, bc=(S.SPFM_CONTACT,) * 6, n=n, u=u)
+    g.init_planar(n[0] * (nx / 2.0 + shift), lam)
+    f0 = g.get_field(to_host=True).double().numpy()
+    dt = 0.5 * g.max_dt(lam=lam, stencil=26, scheme=scheme)   # the sum does not depend on dt
+    g.step(1, lam=lam, dt=dt, stencil=26, scheme=scheme)
+    f1 = g.get_field(to_host=True).double().numpy()
+    g.close()
+    return float(((f1 - f0) / dt).sum() * lam ** 2)
+
+
+def force_oscillation(shifts: int = 16):
+    """Fig. 3: amplitude A (max - min over sub-grid shifts of the ideal profile)
+    of the total grid friction force, the line sum of Eq. 4, against the
+    interface orientation (two rotation paths, r22), for CF, TI_<120> and TI_n
+    at lambda~ = 1 and 3."""
+    from paper_1910_05180_gb300 import spfm as S
+    out = {}
+    u120 = (1.0 / np.sqrt(5.0), 2.0 / np.sqrt(5.0), 0.0)
+    for lam in (1.0, 3.0):
+        for name, sch, u in (("CF", S.SPFM_FD, (0.0, 0.0, 0.0)), ("TI_<120>", S.SPFM_TI_GLOBAL, u120),
+                             ("TI_n", S.SPFM_TI_LOCAL, (0.0, 0.0, 0.0))):
+            rows = []
+            for path, deg, n in orientation_paths():
+                vals = [force_scan_sum(S, n, lam, sch, m / shifts, u) for m in range(shifts)]
+                rows.append({"path": path, "deg": round(deg, 3), "A": max(vals) - min(vals)})
+            out[f"{name}_lam{lam:g}"] = rows
+    return out
+
+
 def shape_relaxation(dev):
     """Sec. 3.3: a cubic particle (half side 12) in 60^3, periodic, relaxed at
     constant volume by spfm_step_conserving for a fixed physical time (250),
@@ -574,6 +626,9 @@ def run_gpu(args):
     friction = None
     if rank == 0 and not args.no_friction:
         friction = friction_1d(dev)
+    force_scan = None
+    if rank == 0 and not args.no_force_scan:
+        force_scan = force_oscillation()
 
     # end to end through the public API from pinned host memory: upload the
     # initial field, E2E_STEPS steps, stats, read the field back
@@ -632,7 +687,7 @@ def run_gpu(args):
                          "avg_launch_ms": avg_kernel_ms,
                          "timed": "per step: stencil kernel + ghost-face kernel (events around 50-step chunks)"},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
-            "batched": batched, "serving": serving, "grain_sphericity": grain, "variants": variants, "bf16_storage": bf16, "shape_relaxation": relax, "friction_1d": friction,
+            "batched": batched, "serving": serving, "grain_sphericity": grain, "variants": variants, "bf16_storage": bf16, "shape_relaxation": relax, "friction_1d": friction, "force_oscillation": force_scan,
             "last_stats": stats_seen[-1] if stats_seen else None,
             "stats_call": {"ms": (total_ms - step_ms) / max(1, len(stats_seen)), "every": STATS_EVERY,
                            "note": "interface stats between step chunks, host round trip included"},

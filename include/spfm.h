@@ -73,8 +73,9 @@ typedef struct {
     int nx, ny, nz;          /* interior cells, each >= 1 */
     int dtype;               /* SPFM_F64 | SPFM_F32 | SPFM_BF16 (BF16 = storage only) */
     int bc[6];               /* per face x-, x+, y-, y+, z-, z+; PERIODIC must be paired */
-    double n[3];             /* unit interface normal: TI coupling direction u and the
-                                CONTACT boundary (Eq. 7); planar position estimator */
+    double n[3];             /* unit interface normal: the CONTACT boundary (Eq. 7), the
+                                planar position estimator and, unless u is given, the
+                                TI_<hkl> coupling direction */
     double gamma[3];         /* shell ponderations gamma_1..3; all 0 selects defaults:
                                 (1,0,0), (1/3,2/3,0), (1/2,1/3,1/6) for 6/18/26 */
     double C_gamma;          /* interface-energy calibration; 0 selects 2/3 */
@@ -83,6 +84,9 @@ typedef struct {
     void *scratch;           /* caller-owned device scratch, scratch_bytes (spfm_layout) */
     size_t scratch_bytes;
     void *stream;            /* cudaStream_t; NULL = legacy default stream */
+    double u[3];             /* TI_<hkl> coupling direction of Eq. 5, a_k = tanh(2 r_k.u /
+                                lambda), when it differs from n (Tab. 2: u || <hkl>);
+                                all 0 selects u = n; else |u| = 1 */
 } spfm_grid_desc;
 
 typedef struct {

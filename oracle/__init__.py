@@ -57,6 +57,7 @@ class _Params(ctypes.Structure):
         ("dt", ctypes.c_double), ("dF", ctypes.c_double),
         ("stencil", ctypes.c_int), ("scheme", ctypes.c_int),
         ("eps_local", ctypes.c_double),
+        ("u", ctypes.c_double * 3),
     ]
 
 
@@ -116,6 +117,7 @@ class Params:
     stencil: int = 6
     scheme: int = TI_GLOBAL
     eps_local: float = 0.0
+    u: tuple = (0.0, 0.0, 0.0)   # TI_<hkl> coupling direction; all zero: n
     extra: dict = field(default_factory=dict)
 
     def c(self) -> _Params:
@@ -131,6 +133,8 @@ class Params:
         p.dt, p.dF = self.dt, self.dF
         p.stencil, p.scheme = self.stencil, self.scheme
         p.eps_local = self.eps_local
+        for i in range(3):
+            p.u[i] = float(self.u[i])
         return p
 
     @property

@@ -209,6 +209,12 @@ void oracle_fill_ghosts(const orc_params *p, const double *phi, double *pad)
 
 /* ------------------------------------------------------------- model terms */
 
+/* the TI_<hkl> coupling direction u of Eq. 5: p->u when set, else the normal */
+static const double *coupling_u(const orc_params *p)
+{
+    return (p->u[0] != 0.0 || p->u[1] != 0.0 || p->u[2] != 0.0) ? p->u : p->n;
+}
+
 /* derivative of h3 = phi^2 (3 - 2 phi) (Sec. 2.1, natural interpolation) */
 static double h3_prime(double phi)
 {
@@ -310,7 +316,7 @@ long oracle_rhs(const orc_params *p, const double *phi, double *R)
     const double Cg = c_gamma_of(p);
     const double lam = p->lambda, dx = p->dx;
     double a_glob[13];
-    oracle_coupling(p->n, lam, dx, a_glob);
+    oracle_coupling(coupling_u(p), lam, dx, a_glob);
 
     double *pad = (double *)malloc(sizeof(double) * (size_t)PADX(p) * PADY(p) * (nz + 2));
     oracle_fill_ghosts(p, phi, pad);
@@ -436,7 +442,7 @@ double oracle_energy(const orc_params *p, const double *phi)
     int nd = oracle_weights(p, w, NULL);
     const double lam = p->lambda, dx = p->dx;
     double a_glob[13];
-    oracle_coupling(p->n, lam, dx, a_glob);
+    oracle_coupling(coupling_u(p), lam, dx, a_glob);
     double *pad = (double *)malloc(sizeof(double) * (size_t)PADX(p) * PADY(p) * (nz + 2));
     oracle_fill_ghosts(p, phi, pad);
     double total = 0.0;

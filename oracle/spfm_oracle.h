@@ -52,13 +52,14 @@ void oracle_shift_x(double *phi, int nx, int ny, int nz, int cells);
 typedef struct {
     int nx, ny, nz;
     int bc[6];
-    double n[3];        /* global normal: TI coupling direction u and contact BC */
+    double n[3];        /* interface normal: contact BC and, unless u is set, the TI coupling direction */
     double gamma[3];    /* shell ponderations; all zero selects the defaults */
     double C_gamma;     /* interface energy calibration; 0 selects 2/3 */
     double M, Gamma, lambda, dx, dt, dF;
     int stencil;        /* 6, 18 or 26 neighbours */
     int scheme;         /* ORC_TI_GLOBAL, ORC_TI_LOCAL, ORC_CF */
     double eps_local;   /* TI_n clamp of phi before inverting the profile; 0 -> 1e-6 */
+    double u[3];        /* TI_<hkl> coupling direction (Tab. 2: u || <hkl>); all 0 -> n */
 } orc_params;
 
 /* Direction table of Tab. 1: out_d[3*k + c] (integers) and out_shell[k]

@@ -57,6 +57,13 @@ void default_gamma(int stencil, const double *given, double *g)
     }
 }
 
+// TI_<hkl> coupling direction: the desc's u when given, else its normal n
+static const double *coupling_dir(const spfm_grid *g)
+{
+    const double *u = g->d.u;
+    return (u[0] != 0.0 || u[1] != 0.0 || u[2] != 0.0) ? u : g->d.n;
+}
+
 int build_model(spfm_grid *g, double M, double Gamma, double lambda, double dx, double dt,
                 double dF, int stencil, int scheme, Model &m)
 {
@@ -84,7 +91,8 @@ int build_model(spfm_grid *g, double M, double Gamma, double lambda, double dx, 
         m.w[k] = k < nd ? m.gamma[d.shell - 1] * nu[d.shell - 1] : 0.0;
         m.ck[k] = k < nd ? m.c_shell[d.shell - 1] : 0.0;
         wsum += m.w[k];
-        const double rn = dx * (d.x * g->d.n[0] + d.y * g->d.n[1] + d.z * g->d.n[2]);
+        const double *u = coupling_dir(g);
+        const double rn = dx * (d.x * u[0] + d.y * u[1] + d.z * u[2]);
         m.a[k] = tanh(2.0 * rn / lambda);   // Eq. 5
     }
     // group equal A_k = a_k^2 of the active directions (TI global)
@@ -205,7 +213,8 @@ void fill_stats_args(const spfm_grid *g, int flags, StatsArgs &a)
     for (int k = 0; k < kMaxTerms; ++k) {
         const Dir d = grid_dir(k);
         a.w[k] = k < nd ? gam[d.shell - 1] * nu[d.shell - 1] : 0.0;
-        a.a[k] = tanh(2.0 * g->dx * (d.x * g->d.n[0] + d.y * g->d.n[1] + d.z * g->d.n[2]) / g->lambda);
+        const double *u = coupling_dir(g);
+        a.a[k] = tanh(2.0 * g->dx * (d.x * u[0] + d.y * u[1] + d.z * u[2]) / g->lambda);
     }
 }
 
@@ -275,6 +284,9 @@ spfm_status spfm_create_grid(const spfm_grid_desc *d, spfm_grid **out)
     const double nn = d->n[0] * d->n[0] + d->n[1] * d->n[1] + d->n[2] * d->n[2];
     if (!(fabs(nn - 1.0) < 1e-9))
         return fail(nullptr, SPFM_EINVAL, "spfm_create_grid: |n| = %g, must be 1", sqrt(nn));
+    const double uu = d->u[0] * d->u[0] + d->u[1] * d->u[1] + d->u[2] * d->u[2];
+    if (!(uu == 0.0 || fabs(uu - 1.0) < 1e-9))
+        return fail(nullptr, SPFM_EINVAL, "spfm_create_grid: |u| = %g, must be 0 (u = n) or 1", sqrt(uu));
     for (int b = 0; b < 2; ++b)
         if (!d->field[b] || ((uintptr_t)d->field[b] & 15))
             return fail(nullptr, SPFM_EINVAL, "spfm_create_grid: field[%d] NULL or not 16-byte aligned", b);

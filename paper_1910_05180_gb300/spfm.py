@@ -53,6 +53,7 @@ class GridDesc(ctypes.Structure):
         ("scratch", ctypes.c_void_p),
         ("scratch_bytes", ctypes.c_size_t),
         ("stream", ctypes.c_void_p),
+        ("u", ctypes.c_double * 3),
     ]
 
 
@@ -240,13 +241,14 @@ class Grid:
 
     def __init__(self, nx, ny, nz, dtype=SPFM_F32, bc=(SPFM_PERIODIC,) * 6, n=(1.0, 0.0, 0.0),
                  gamma=(0.0, 0.0, 0.0), C_gamma=0.0, center=(0.0, 0.0, 0.0), device="cuda",
-                 stream=None):
+                 stream=None, u=(0.0, 0.0, 0.0)):
         d = GridDesc()
         d.nx, d.ny, d.nz, d.dtype = int(nx), int(ny), int(nz), int(dtype)
         for i in range(6):
             d.bc[i] = int(bc[i])
         for i in range(3):
             d.n[i], d.gamma[i], d.center[i] = float(n[i]), float(gamma[i]), float(center[i])
+            d.u[i] = float(u[i])
         d.C_gamma = float(C_gamma)
         pitch, xoff, fbytes, sbytes = spfm_layout(d)
         self.pitch, self.x_off, self.field_bytes, self.scratch_bytes = pitch, xoff, fbytes, sbytes

@@ -81,3 +81,27 @@ def test_1d_frame_keeps_the_interface_and_its_velocity():
     assert offset <= -8                        # the frame moved: the interface travelled cells
     v = np.polyfit(ts, xs, 1)[0]
     assert abs(v / (-dF) - 1.0) < 1e-3
+
+
+@pytest.mark.parametrize("scheme,oscheme", [(S.SPFM_FD, O.CF), (S.SPFM_TI_GLOBAL, O.TI_GLOBAL),
+                                            (S.SPFM_TI_LOCAL, O.TI_LOCAL)])
+def test_force_scan_line_sum_matches_oracle(scheme, oscheme):
+    """Fig. 3 setup: the line sum of Eq. 4 for the ideal profile on 300 x 1 x 1
+    with contact faces, from one FP64 GPU step, equals the oracle's RHS sum;
+    TI_<120> vanishes for a normal of the <120> family, TI_n for any normal
+    (to the level of its profile clamp at phi = 1e-6)."""
+    import bench
+    u120 = (1.0 / np.sqrt(5.0), 2.0 / np.sqrt(5.0), 0.0)
+    for n in ((0.8944271909999159, 0.0, 0.4472135954999579), (0.8, 0.36, 0.48)):
+        for shift in (0.0, 0.37):
+            lam = 1.5
+            u = u120 if scheme == S.SPFM_TI_GLOBAL else (0.0, 0.0, 0.0)
+            got = bench.force_scan_sum(S, n, lam, scheme, shift, u)
+            p = O.Params(300, 1, 1, bc=(O.CONTACT,) * 6, n=n, u=u, lam=lam, stencil=26, scheme=oscheme)
+            R, _ = O.rhs(p, O.init_planar(p, n[0] * (150.0 + shift)))
+            want = float(R.sum() * lam ** 2)
+            assert abs(got - want) <= 1e-9 * max(1.0, abs(want)), (n, shift, got, want)
+            if scheme == S.SPFM_TI_GLOBAL and n[1] == 0.0:
+                assert abs(got) < 1e-9
+            if scheme == S.SPFM_TI_LOCAL:
+                assert abs(got) < 1e-5

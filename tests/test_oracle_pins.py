@@ -508,3 +508,16 @@ def test_conserving_force_on_a_sphere_is_gibbs_thomson():
             errs.append(abs(dF[0] / (2 * G / R) - 1))
     assert abs(errs[0] - errs[1]) < 1e-12 and abs(errs[2] - errs[3]) < 1e-12
     assert errs[0] < 0.015 and errs[2] < 0.004 and errs[0] > 3.0 * errs[2]
+
+
+def test_ti_hkl_restores_ti_for_the_whole_family():
+    """Tab. 2: with couplings a_k(u), u || <hkl>, TI holds for every interface
+    normal of the <hkl> family (the potential's sum over directions depends only
+    on the multiset of (w_k, |a_k|), which the cubic symmetries of the stencil
+    preserve), not for other normals."""
+    u = _unit([1, 2, 0])
+    for n, fixed in ((_unit([2, 0, 1]), True), (_unit([0, -1, 2]), True), (_unit([1, 1, 0]), False)):
+        p = O.Params(26, 18, 16, bc=(O.CONTACT,) * 6, n=tuple(n), u=tuple(u), lam=2.0, stencil=26)
+        phi = O.init_planar(p, float(n @ [12.5, 8.5, 7.5]))
+        R, _ = O.rhs(p, phi)
+        assert (np.abs(R).max() < 1e-12) == fixed, (n, np.abs(R).max())
