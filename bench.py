@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-relax", action="store_true", help="skip the constant-volume shape relaxation")
     ap.add_argument("--no-friction", action="store_true", help="skip the 1D friction study")
     ap.add_argument("--no-force-scan", action="store_true", help="skip the force-oscillation scan")
+    ap.add_argument("--no-kinetic", action="store_true", help="skip the 3D kinetic-anisotropy study")
     ap.add_argument("--n", type=int, default=512, help="grid edge")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -374,18 +375,87 @@ def friction_1d(dev, steps: int = 24000, window: int = 200):
     return out
 
 
-def orientation_paths():
-    """The two rotation paths of the force-oscillation scan: about [001] from
-    [100] to [110], and from [100] towards [011] up to [111] (reading r22)."""
+def orientation_paths(n_angles: int = 10, top: float = 81.0):
+    """The two rotation paths of Figs. 3 and 10 (reading r22): the normal turns
+    away from [100] about the [001] axis, n = (cos t, sin t, 0), and about the
+    [011] axis, n = (cos t, sin t / sqrt 2, -sin t / sqrt 2), for t from 0 to
+    `top` degrees, plus the [210] normal (26.57 degrees, a <120> member) on the
+    first path and [11-1] (54.74 degrees, <111>) on the second."""
     out = []
-    # 0..45 degrees plus the [210] normal itself (atan(1/2) = 26.57 degrees), a <120> member
-    for deg in sorted(list(np.linspace(0.0, 45.0, 10)) + [float(np.degrees(np.arctan(0.5)))]):
+    grid = list(np.linspace(0.0, top, n_angles))
+    for deg in sorted(grid + [float(np.degrees(np.arctan(0.5)))]):
         t = np.radians(deg)
         out.append(("001", float(deg), (float(np.cos(t)), float(np.sin(t)), 0.0)))
-    for deg in np.linspace(0.0, np.degrees(np.arctan(np.sqrt(2.0))), 10):
+    for deg in sorted(grid + [float(np.degrees(np.arctan(np.sqrt(2.0))))]):
         t = np.radians(deg)
         out.append(("011", float(deg), (float(np.cos(t)), float(np.sin(t) / np.sqrt(2.0)),
-                                        float(np.sin(t) / np.sqrt(2.0)))))
+                                        float(-np.sin(t) / np.sqrt(2.0)))))
+    return out
+
+
+def kinetic_anisotropy(dev, models=None, lams=(4.0, 2.0, 1.0), travel: float = 4.0, window: int = 100):
+    """Fig. 10: relative error of the stationary velocity of planar interfaces
+    against their orientation on 120 x 10 x 10 (contact faces, Eq. 7), with
+    dF = dF0 cos(t), dF0~ = 0.1, so that the x component of the velocity is the
+    same for every orientation.  Models: CF, TI_<hkl> for u || [100], [110],
+    [111], [120], and TI_n, all with h3.  lambda~ = 0.5 (in the paper's figure)
+    is left out: its stable dt for TI_n is 9e-6, some 10^7 steps per run.
+    dt = min(0.01, dt_max / 2); the run
+    lasts until the interface has moved `travel` cells along x; the velocity is
+    the slope of the position over the last 60 % of the run, the oscillation the
+    spread of the window velocities."""
+    import torch
+    from paper_1910_05180_gb300 import spfm as S
+    unit = lambda v: tuple(float(x) for x in np.array(v, float) / np.linalg.norm(v))
+    if models is None:
+        models = [("CF", S.SPFM_FD, (0.0, 0.0, 0.0)), ("TI_<100>", S.SPFM_TI_GLOBAL, unit([1, 0, 0])),
+                  ("TI_<110>", S.SPFM_TI_GLOBAL, unit([1, 1, 0])), ("TI_<111>", S.SPFM_TI_GLOBAL, unit([1, 1, 1])),
+                  ("TI_<120>", S.SPFM_TI_GLOBAL, unit([1, 2, 0])), ("TI_n", S.SPFM_TI_LOCAL, (0.0, 0.0, 0.0))]
+    dF0, shape = 0.1, (120, 10, 10)
+    paths = orientation_paths(8, 70.0)
+    out = {}
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        for lam in lams:
+            for name, sch, u in models:
+                grids, args, meta = [], [], []
+                for path, deg, n in paths:
+                    dF = dF0 * np.cos(np.radians(deg))
+                    g = S.Grid(*shape, dtype=S.SPFM_F32, bc=(S.SPFM_CONTACT,) * 6, n=n, u=u, stream=stream)
+                    dt = min(0.01, 0.5 * g.max_dt(lam=lam, dF=dF, stencil=26, scheme=sch))
+                    g.init_planar(float(np.dot(n, (np.array(shape) - 1) / 2.0)) + 2.5, lam)
+                    grids.append(g)
+                    args.append(S.step_args(lam=lam, dt=dt, dF=dF, stencil=26, scheme=sch))
+                    meta.append((path, deg, dF, dt))
+                dt_min = min(m[3] for m in meta)
+                steps = int(np.ceil(travel / (dF0 * dt_min) / window)) * window
+                pos = [[] for _ in grids]
+                nwin = steps // window
+                b = S.Batch(grids, stream=stream) if sch != S.SPFM_TI_LOCAL else None
+                for w in range(nwin):
+                    if b is not None:
+                        b.step(window, args)
+                        st = b.stats()
+                    else:
+                        st = []
+                        for g, a in zip(grids, args):
+                            g.step(window, lam=a.lam, dt=a.dt, dF=a.dF, stencil=26, scheme=sch)
+                            st.append(g.stats())
+                    if w >= int(0.4 * nwin):
+                        for i, sti in enumerate(st):
+                            pos[i].append(((w + 1) * window * meta[i][3], sti["position"]))
+                if b is not None:
+                    b.close()
+                rows = []
+                for i, (path, deg, dF, dt) in enumerate(meta):
+                    t, x = np.array(pos[i]).T
+                    v = np.polyfit(t, x, 1)[0]
+                    vw = np.diff(x) / np.diff(t)
+                    rows.append({"path": path, "deg": round(deg, 2), "err_mean": float(abs(v / (-dF) - 1.0)),
+                                 "err_osc": float((vw.max() - vw.min()) / dF)})
+                for g in grids:
+                    g.close()
+                out[f"{name}_lam{lam:g}"] = {"steps": steps, "rows": rows}
     return out
 
 
@@ -629,6 +699,9 @@ def run_gpu(args):
     force_scan = None
     if rank == 0 and not args.no_force_scan:
         force_scan = force_oscillation()
+    kinetic = None
+    if rank == 0 and not args.no_kinetic:
+        kinetic = kinetic_anisotropy(dev)
 
     # end to end through the public API from pinned host memory: upload the
     # initial field, E2E_STEPS steps, stats, read the field back
@@ -687,7 +760,7 @@ def run_gpu(args):
                          "avg_launch_ms": avg_kernel_ms,
                          "timed": "per step: stencil kernel + ghost-face kernel (events around 50-step chunks)"},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
-            "batched": batched, "serving": serving, "grain_sphericity": grain, "variants": variants, "bf16_storage": bf16, "shape_relaxation": relax, "friction_1d": friction, "force_oscillation": force_scan,
+            "batched": batched, "serving": serving, "grain_sphericity": grain, "variants": variants, "bf16_storage": bf16, "shape_relaxation": relax, "friction_1d": friction, "force_oscillation": force_scan, "kinetic_anisotropy": kinetic,
             "last_stats": stats_seen[-1] if stats_seen else None,
             "stats_call": {"ms": (total_ms - step_ms) / max(1, len(stats_seen)), "every": STATS_EVERY,
                            "note": "interface stats between step chunks, host round trip included"},

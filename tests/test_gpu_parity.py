@@ -16,7 +16,8 @@ from paper_1910_05180_gb300 import workloads as WL
 pytestmark = pytest.mark.gpu
 
 TOL = {S.SPFM_F64: 1e-12, S.SPFM_F32: 2e-5}
-SCHEME_O = {S.SPFM_TI_GLOBAL: O.TI_GLOBAL, S.SPFM_FD: O.CF, S.SPFM_TI_LOCAL: O.TI_LOCAL}
+SCHEME_O = {S.SPFM_TI_GLOBAL: O.TI_GLOBAL, S.SPFM_FD: O.CF, S.SPFM_TI_LOCAL: O.TI_LOCAL,
+            S.SPFM_FD_H5: O.CF_H5, S.SPFM_FD_HABEL: O.CF_HABEL}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -78,6 +79,13 @@ CASES = [
     ((37, 21, 19), (S.SPFM_CONTACT,) * 6, 6, S.SPFM_FD),
     ((5, 3, 2), (S.SPFM_CONTACT,) * 6, 26, S.SPFM_TI_GLOBAL),
     ((1, 1, 40), (S.SPFM_PERIODIC,) * 4 + (S.SPFM_NOFLUX,) * 2, 26, S.SPFM_TI_GLOBAL),
+    # degenerate and tile-crossing extents
+    ((1, 1, 1), (S.SPFM_PERIODIC,) * 6, 26, S.SPFM_TI_GLOBAL),
+    ((3, 1, 1), (S.SPFM_CONTACT,) * 6, 26, S.SPFM_FD),
+    ((1, 50, 1), (S.SPFM_NOFLUX,) * 6, 18, S.SPFM_TI_GLOBAL),
+    ((130, 2, 3), (S.SPFM_PERIODIC,) * 2 + (S.SPFM_CONTACT,) * 4, 26, S.SPFM_TI_LOCAL),
+    ((65, 17, 33), (S.SPFM_CONTACT,) * 6, 26, S.SPFM_FD_HABEL),
+    ((64, 16, 32), (S.SPFM_CONTACT,) * 6, 26, S.SPFM_FD_H5),
 ]
 
 
