@@ -138,7 +138,8 @@ def measured_hbm_peak():
 
 # the sources that decide the stencil kernel's code (its traffic record is
 # dropped as soon as one of them changes)
-STEP_SOURCES = ("spfm_internal.h", "step_kernel.cuh", "step_f32.cu", "step_f64.cu", "step_bf16.cu")
+STEP_SOURCES = ("spfm_internal.h", "step_kernel.cuh", "step_f32.cu", "step_f64.cu", "step_bf16.cu",
+                "step_f32_img.cu", "step_f64_img.cu", "step_bf16_img.cu")
 
 
 def source_hash(names=STEP_SOURCES):
@@ -636,13 +637,14 @@ def run_gpu(args):
     clocks = ClockSampler(dev.index if dev.index is not None else 0)
     clocks.start()
     launches = 0
+    per_step = g.kernels_per_step()
     stats_seen = []
     t_start.record(stream)
     for (e0, e1), n in zip(ev, chunks):
         e0.record(stream)
         g.step(n, **kw)
         e1.record(stream)
-        launches += 2 * n      # stencil kernel + ghost-face kernel per step
+        launches += per_step * n   # stencil kernel (+ ghost-face kernel unless it writes the images)
         if n == STATS_EVERY:
             stats_seen.append(g.stats())
             launches += 2
@@ -758,7 +760,9 @@ def run_gpu(args):
                          "traffic": profiled_traffic(kernel_key),
                          "kernel": "spfm_step_kernel", "bytes_per_update": bpu,
                          "avg_launch_ms": avg_kernel_ms,
-                         "timed": "per step: stencil kernel + ghost-face kernel (events around 50-step chunks)"},
+                         "timed": ("per step: stencil kernel, which writes the periodic ghost images itself"
+                                   if per_step == 1 else "per step: stencil kernel + ghost-face kernel")
+                                  + " (events around 50-step chunks)"},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
             "batched": batched, "serving": serving, "grain_sphericity": grain, "variants": variants, "bf16_storage": bf16, "shape_relaxation": relax, "friction_1d": friction, "force_oscillation": force_scan, "kinetic_anisotropy": kinetic,
             "last_stats": stats_seen[-1] if stats_seen else None,

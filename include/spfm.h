@@ -29,10 +29,13 @@
  *  - Field layout in HBM: x fastest, with a one-cell ghost layer on every
  *    face.  Interior cell (i, j, k), 0 <= i < nx etc., is
  *      field[((k + 1) * (ny + 2) + (j + 1)) * pitch_x + x_off + i],
- *    ghost cells sit at i = -1, nx, j = -1, ny, k = -1, nz.  x_off is 16 bytes
- *    worth of elements (2 FP64, 4 FP32, 8 BF16), pitch_x a 16-byte multiple
- *    >= x_off + nx + 1, so every interior row starts 16-byte aligned.  The
- *    base pointer must be 16-byte aligned.  The library keeps the ghosts
+ *    ghost cells sit at i = -1, nx, j = -1, ny, k = -1, nz.  x_off is 32 bytes
+ *    worth of elements (4 FP64, 8 FP32, 16 BF16), pitch_x a 32-byte multiple
+ *    >= x_off + nx + 1, so every interior row starts on a 32-byte boundary
+ *    relative to the base pointer.  The base pointer must be 16-byte aligned
+ *    (256-byte alignment, as cudaMalloc gives, keeps whole 32-byte sectors).
+ *    The elements left of x_off - 1 and right of x_off + nx are padding; the
+ *    library may write them.  The library keeps the ghosts
  *    consistent with the boundary conditions; use spfm_get_field /
  *    spfm_set_field to exchange dense interior arrays.
  *  - Launches are asynchronous on the grid's stream.  spfm_interface_stats,
@@ -211,6 +214,11 @@ spfm_status spfm_get_field(spfm_grid *g, void *dst, int dst_on_host);
 spfm_status spfm_set_field(spfm_grid *g, const void *src, int src_on_host);
 /* Index (0 or 1) of the buffer holding the current field. */
 int spfm_current(const spfm_grid *g);
+/* Kernel launches of one spfm_step step on g: 1 when every face is periodic,
+ * nx is a whole number (>= 2) of 32-byte sectors and ny >= 2 (the step kernel
+ * then writes the periodic ghost images of its new cells itself), else 2 (the
+ * step kernel and the ghost-face refresh); -1 for NULL. */
+int spfm_kernels_per_step(const spfm_grid *g);
 
 /* Message of the last failure on g (or of this thread when g is NULL). */
 const char *spfm_last_error(const spfm_grid *g);

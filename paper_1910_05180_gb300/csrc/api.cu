@@ -186,6 +186,17 @@ int refresh_ghosts(spfm_grid *g, double lambda, double dx)
     return SPFM_OK;
 }
 
+// Every face periodic, nx a whole number (>= 2) of 32-byte sectors and ny >= 2:
+// the step kernel writes the ghost images of its new cells itself (kImages),
+// its x images as whole sectors of the row pads.
+bool writes_own_images(const spfm_grid *g)
+{
+    for (int f = 0; f < 6; ++f)
+        if (g->d.bc[f] != SPFM_PERIODIC) return false;
+    const int per32 = (int)(32 / g->elem);
+    return g->d.nx % per32 == 0 && g->d.nx >= 2 * per32 && g->d.ny >= 2 && g->geom.off == per32;
+}
+
 int *err_word(const spfm_grid *g)
 {
     return (int *)((char *)g->d.scratch + scratch_err_offset());
@@ -254,10 +265,10 @@ spfm_status spfm_layout(const spfm_grid_desc *d, size_t *pitch_x, size_t *x_offs
         return fail(nullptr, SPFM_EINVAL, "spfm_layout: sizes must be >= 1");
     if (d->dtype != SPFM_F64 && d->dtype != SPFM_F32 && d->dtype != SPFM_BF16)
         return fail(nullptr, SPFM_EINVAL, "spfm_layout: unknown dtype %d", d->dtype);
-    const size_t es = elem_size(d->dtype), per16 = 16 / es;
-    const size_t px = (per16 + d->nx + 1 + per16 - 1) / per16 * per16;
+    const size_t es = elem_size(d->dtype), per32 = 32 / es;
+    const size_t px = (per32 + d->nx + 1 + per32 - 1) / per32 * per32;
     if (pitch_x) *pitch_x = px;
-    if (x_offset) *x_offset = per16;
+    if (x_offset) *x_offset = per32;
     if (field_bytes) *field_bytes = px * (size_t)(d->ny + 2) * (size_t)(d->nz + 2) * es;
     if (scratch_bytes) *scratch_bytes = grid_scratch_bytes();
     return SPFM_OK;
@@ -326,6 +337,8 @@ spfm_status spfm_set_stream(spfm_grid *g, void *stream)
 
 int spfm_current(const spfm_grid *g) { return g ? g->cur : -1; }
 
+int spfm_kernels_per_step(const spfm_grid *g) { return g ? (writes_own_images(g) ? 1 : 2) : -1; }
+
 static spfm_status init_common(spfm_grid *g, InitArgs &a, double lambda, double dx)
 {
     if (!(lambda > 0.0) || !(dx > 0.0))
@@ -386,22 +399,27 @@ spfm_status spfm_step(spfm_grid *g, int n_steps, double M, double Gamma, double 
     Model m;
     spfm_status st = build_model(g, M, Gamma, lambda, dx, dt, dF, stencil, scheme, m);
     if (st != SPFM_OK) return st;
-    const LaunchCfg cfg{stencil, scheme};
+    LaunchCfg cfg{stencil, scheme, 0};
     cudaStream_t s = stream_of(g);
     if (n_steps > 0 && (g->ghosts_dirty || g->ghost_lambda != lambda || g->ghost_dx != dx)) {
         st = refresh_ghosts(g, lambda, dx);
         if (st != SPFM_OK) return st;
     }
+    // all faces periodic and rows of whole 32-byte sectors: each step writes the
+    // periodic images of its new cells, and no face kernel runs between steps
+    const bool images = writes_own_images(g);
+    auto mode_of = [&](int i) { return images ? kWaitAll | kImages : (i == 0 ? kWaitAll : kWaitFaces); };
     int *err = err_word(g);
     if (g->d.dtype == SPFM_F64) {
         StepCoef<double> c;
         fill_coef<double>(g, m, dt, stencil, c);
         set_local_coef<double>(c, lambda, dx);
         for (int i = 0; i < n_steps; ++i) {
+            cfg.mode = mode_of(i);
             cudaError_t e = launch_step_f64(c, (const double *)g->d.field[g->cur],
                                             (double *)g->d.field[1 - g->cur], err, cfg, &g->tma,
                                             g->cur, s);
-            if (e == cudaSuccess)
+            if (e == cudaSuccess && !images)
                 e = launch_fill_ghosts(g->geom, g->d.dtype, m.aface, g->d.field[1 - g->cur], s, 1);
             if (e != cudaSuccess) return cuda_fail(g, e, "spfm_step");
             g->cur ^= 1;
@@ -411,6 +429,7 @@ spfm_status spfm_step(spfm_grid *g, int n_steps, double M, double Gamma, double 
         fill_coef<float>(g, m, dt, stencil, c);
         set_local_coef<float>(c, lambda, dx);
         for (int i = 0; i < n_steps; ++i) {
+            cfg.mode = mode_of(i);
             cudaError_t e;
             if (g->d.dtype == SPFM_F32)
                 e = launch_step_f32(c, (const float *)g->d.field[g->cur], (float *)g->d.field[1 - g->cur],
@@ -419,7 +438,7 @@ spfm_status spfm_step(spfm_grid *g, int n_steps, double M, double Gamma, double 
                 e = launch_step_bf16(c, (const __nv_bfloat16 *)g->d.field[g->cur],
                                      (__nv_bfloat16 *)g->d.field[1 - g->cur], err, cfg, &g->tma,
                                      g->cur, s);
-            if (e == cudaSuccess)
+            if (e == cudaSuccess && !images)
                 e = launch_fill_ghosts(g->geom, g->d.dtype, m.aface, g->d.field[1 - g->cur], s, 1);
             if (e != cudaSuccess) return cuda_fail(g, e, "spfm_step");
             g->cur ^= 1;
@@ -447,7 +466,7 @@ spfm_status spfm_step_conserving(spfm_grid *g, int n_steps, double M, double Gam
     Model m;
     spfm_status st = build_model(g, M, Gamma, lambda, dx, dt, 0.0, stencil, scheme, m);
     if (st != SPFM_OK) return st;
-    const LaunchCfg cfg{stencil, scheme};
+    LaunchCfg cfg{stencil, scheme, 0};
     cudaStream_t s = stream_of(g);
     if (n_steps > 0 && (g->ghosts_dirty || g->ghost_lambda != lambda || g->ghost_dx != dx)) {
         st = refresh_ghosts(g, lambda, dx);
@@ -467,6 +486,7 @@ spfm_status spfm_step_conserving(spfm_grid *g, int n_steps, double M, double Gam
     }
     for (int i = 0; i < n_steps; ++i) {
         void *src = g->d.field[g->cur], *dst = g->d.field[1 - g->cur];
+        cfg.mode = i == 0 ? kWaitAll : kWaitFaces;   // the face kernel follows the correction
         cudaError_t e;
         if (g->d.dtype == SPFM_F64)
             e = launch_step_f64(cd, (const double *)src, (double *)dst, err, cfg, &g->tma, g->cur, s);

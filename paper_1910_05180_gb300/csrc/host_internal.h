@@ -50,6 +50,7 @@ int build_model(spfm_grid *g, double M, double Gamma, double lambda, double dx, 
 cudaStream_t stream_of(const spfm_grid *g);
 int refresh_ghosts(spfm_grid *g, double lambda, double dx);
 int *err_word(const spfm_grid *g);
+bool writes_own_images(const spfm_grid *g);
 void fill_stats_args(const spfm_grid *g, int flags, spfm::StatsArgs &a);
 void stats_from_reduction(const spfm_grid *g, const double *h, int energy, spfm_stats *out);
 

@@ -43,12 +43,13 @@ __host__ __device__ inline Dir grid_dir(int k)
 // Geometry of one grid buffer as the kernels see it.  Every buffer carries a
 // one-cell ghost layer: interior cell (i, j, k), i in [0, nx), sits at
 //   ((k + 1) * (ny + 2) + (j + 1)) * pitch + off + i,
-// ghosts at i = -1, nx, j = -1, ny, k = -1, nz.  off = 16 bytes of elements, so
-// interior rows start 16-byte aligned; pitch is a 16-byte multiple >= off + nx + 1.
+// ghosts at i = -1, nx, j = -1, ny, k = -1, nz.  off = 32 bytes of elements, so
+// interior rows start on a 32-byte sector, and the x ghosts sit in sectors of
+// their own; pitch is a 32-byte multiple >= off + nx + 1.
 struct GridGeom {
     int nx, ny, nz;
     int pitch;          // elements per padded row
-    int off;            // x offset of interior cell 0 (16 bytes of elements)
+    int off;            // x offset of interior cell 0 (32 bytes of elements)
     long long plane;    // pitch * (ny + 2)
     int bc[6];          // SPFM_PERIODIC / NOFLUX / CONTACT per face
 };
@@ -119,7 +120,15 @@ __host__ __device__ inline T contact_shift(T v, T a)
 struct LaunchCfg {
     int stencil;   // 6, 18, 26
     int scheme;    // SPFM_TI_GLOBAL, SPFM_TI_LOCAL, SPFM_FD
+    int mode;      // kWaitFaces | kWaitAll | kImages
 };
+
+// How a step launch sits in the stream (programmatic dependent launch):
+//   kWaitFaces  the previous kernel refreshes src's ghosts: boxes touching a face wait for it
+//   kWaitAll    every box waits for the previous kernel
+//   kImages     all faces periodic: the step writes the ghost images of its new cells
+//               itself (no face kernel follows) and lets the next step launch early
+constexpr int kWaitFaces = 1, kWaitAll = 2, kImages = 4;
 
 // TMA tensor maps of a grid's two field buffers, encoded on first use (tma.cu).
 struct TmaCache {
@@ -137,7 +146,8 @@ int encode_field_map(CUtensorMap *map, const GridGeom &g, int dtype, const void 
 const CUtensorMap *cached_map(TmaCache *cache, int which, const GridGeom &g, int dtype,
                               const void *base, int box_x, int box_y);
 
-// One explicit step src -> dst of one grid (step_f32.cu / step_f64.cu / step_bf16.cu).
+// One explicit step src -> dst of one grid (step_f32.cu / step_f64.cu / step_bf16.cu;
+// with kImages in cfg.mode the *_img.cu kernels).
 // err: device word that a kernel sets when one of its bounded waits gives up.
 // tma: map cache of the grid (NULL: row-wise bulk copies); which: index of src.
 cudaError_t launch_step_f32(const StepCoef<float> &c, const float *src, float *dst, int *err,
@@ -147,6 +157,14 @@ cudaError_t launch_step_f64(const StepCoef<double> &c, const double *src, double
 cudaError_t launch_step_bf16(const StepCoef<float> &c, const __nv_bfloat16 *src,
                              __nv_bfloat16 *dst, int *err, LaunchCfg cfg, TmaCache *tma, int which,
                              cudaStream_t st);
+// the same, for all-periodic grids whose step writes its own ghost images (kImages)
+cudaError_t launch_step_f32_img(const StepCoef<float> &c, const float *src, float *dst, int *err,
+                                LaunchCfg cfg, TmaCache *tma, int which, cudaStream_t st);
+cudaError_t launch_step_f64_img(const StepCoef<double> &c, const double *src, double *dst, int *err,
+                                LaunchCfg cfg, TmaCache *tma, int which, cudaStream_t st);
+cudaError_t launch_step_bf16_img(const StepCoef<float> &c, const __nv_bfloat16 *src,
+                                 __nv_bfloat16 *dst, int *err, LaunchCfg cfg, TmaCache *tma, int which,
+                                 cudaStream_t st);
 
 // Initial ideal profiles and FP64 diagnostics (stats.cu).
 struct InitArgs {

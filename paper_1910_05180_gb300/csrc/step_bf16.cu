@@ -5,9 +5,10 @@ namespace spfm {
 cudaError_t launch_step_bf16(const StepCoef<float> &c, const __nv_bfloat16 *src, __nv_bfloat16 *dst, int *err,
                             LaunchCfg cfg, TmaCache *tma, int which, cudaStream_t st)
 {
+    if (cfg.mode & kImages) return launch_step_bf16_img(c, src, dst, err, cfg, tma, which, st);
     using Sh = TileShape<__nv_bfloat16, float, 8, 16>;
     const CUtensorMap *map = cached_map(tma, which, c.g, SPFM_BF16, src, Sh::SW, Sh::ROWS);
-    return launch_step_t<__nv_bfloat16, float, 8, 16>(c, src, dst, err, cfg, map, st);
+    return launch_step_t<__nv_bfloat16, float, 8, 16, false>(c, src, dst, err, cfg, map, st);
 }
 
 size_t batch_grid_bytes_bf16() { return sizeof(BatchGrid<float>); }

@@ -13,9 +13,10 @@ namespace spfm {
 cudaError_t launch_step_f32(const StepCoef<float> &c, const float *src, float *dst, int *err,
                             LaunchCfg cfg, TmaCache *tma, int which, cudaStream_t st)
 {
+    if (cfg.mode & kImages) return launch_step_f32_img(c, src, dst, err, cfg, tma, which, st);
     using Sh = TileShape<float, float, SPFM_F32_TX, SPFM_F32_TY>;
     const CUtensorMap *map = cached_map(tma, which, c.g, SPFM_F32, src, Sh::SW, Sh::ROWS);
-    return launch_step_t<float, float, SPFM_F32_TX, SPFM_F32_TY>(c, src, dst, err, cfg, map, st);
+    return launch_step_t<float, float, SPFM_F32_TX, SPFM_F32_TY, false>(c, src, dst, err, cfg, map, st);
 }
 
 size_t batch_grid_bytes_f32() { return sizeof(BatchGrid<float>); }

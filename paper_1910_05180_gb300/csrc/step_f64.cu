@@ -5,9 +5,10 @@ namespace spfm {
 cudaError_t launch_step_f64(const StepCoef<double> &c, const double *src, double *dst, int *err,
                             LaunchCfg cfg, TmaCache *tma, int which, cudaStream_t st)
 {
+    if (cfg.mode & kImages) return launch_step_f64_img(c, src, dst, err, cfg, tma, which, st);
     using Sh = TileShape<double, double, 16, 16>;
     const CUtensorMap *map = cached_map(tma, which, c.g, SPFM_F64, src, Sh::SW, Sh::ROWS);
-    return launch_step_t<double, double, 16, 16>(c, src, dst, err, cfg, map, st);
+    return launch_step_t<double, double, 16, 16, false>(c, src, dst, err, cfg, map, st);
 }
 
 size_t batch_grid_bytes_f64() { return sizeof(BatchGrid<double>); }

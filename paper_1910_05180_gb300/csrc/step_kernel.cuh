@@ -13,12 +13,16 @@
 // march, and NS-1 planes stay in flight per CTA.  Every wait is bounded: on
 // timeout the thread sets the error word and leaves.
 //
-// Boundary conditions.  The kernel reads the ghost layer and writes interior
-// cells only; a face kernel (boundary.cu) refreshes the ghosts of the new
-// field after each step, so the hot path holds no boundary logic.  Under
-// programmatic dependent launch the next step starts while that kernel runs:
-// tiles whose halo touches a face wait for it (griddepcontrol.wait), interior
-// tiles do not.
+// Boundary conditions.  The kernel reads the ghost layer.  In general it
+// writes interior cells only and a face kernel (boundary.cu) refreshes the
+// ghosts of the new field after each step; under programmatic dependent launch
+// the next step starts while that kernel runs, and tiles whose halo touches a
+// face wait for it (griddepcontrol.wait), interior tiles do not.  When every
+// face is periodic and a row is a whole number of 32-byte sectors, the ghosts
+// are plain periodic images: the thread that writes a cell next to a face also
+// writes its image(s) on the far side (x images as whole 32-byte sectors of
+// the row pads, two threads a sector), so no face kernel runs, and the next
+// step waits for this one in every tile.
 //
 // Arithmetic.  From each plane every thread forms, for its cells,
 //   C  = phi at the cell,
@@ -445,19 +449,39 @@ __device__ __forceinline__ void get_row(const S *r, typename Pk<T>::P *c, typena
     }
 }
 
+// Periodic images across the z faces of the 16 bytes of new cells at
+// (x.., y, z) of an all-periodic grid: z + nz on plane 0, z - nz on plane
+// nz - 1, each also shifted by the cells' x and y images (edges, corners).
+template <class S>
+__device__ __forceinline__ void store_z_images(const GridGeom &g, S *dst, int x, int y, int z, uint4 v,
+                                               int ximg, int yimg)
+{
+    const bool zu[2] = {z == 0, z == g.nz - 1};
+    const int zs[2] = {g.nz, -g.nz};
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        if (!zu[c]) continue;
+        S *p = dst + cell_index(g, x, y, z + zs[c]);
+        *reinterpret_cast<uint4 *>(p) = v;
+        if (ximg) *reinterpret_cast<uint4 *>(p + ximg) = v;
+        if (yimg) *reinterpret_cast<uint4 *>(p + yimg) = v;
+        if (ximg && yimg) *reinterpret_cast<uint4 *>(p + yimg + ximg) = v;
+    }
+}
+
 // KIND: 0 = CF potential; 1..4 = TI global with exactly KIND coupling groups;
 // 5 = TI global with up to 13 groups (count read at run time)
 // One tile (bx, by) of planes zc0..zc1-1.  The stage ring continues across the
 // tiles a CTA processes: plane i of this tile is ring slot base + i.  The
 // producer waits for its copies in flight before returning when drain is set.
 // Returns false when a bounded wait gave up (the error word is set).
-template <class S, class T, int STENCIL, int KIND, int TX, int TY, int RPT_>
+template <class S, class T, int STENCIL, int KIND, int TX, int TY, int RPT_, bool IMG = false>
 __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T> &PC,
                                           const S *__restrict__ src, S *__restrict__ dst,
                                           int *__restrict__ err, const CUtensorMap *tmap, int bx,
                                           int by, int zc0, int zc1, S *__restrict__ stages,
                                           uint64_t *full, uint64_t *empty, int base, bool drain,
-                                          bool wait_prior = false)
+                                          int mode = 0)
 {
     using Sh = TileShape<S, T, TX, TY, RPT_>;
     using K = Pk<T>;
@@ -475,11 +499,15 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
     if (tid >= Sh::NCONS) {
         // ------------------------------------------------------- producer warp
         if (tid != Sh::NCONS) return true;
-        // The kernel may start while the previous launch (the ghost-face refresh
-        // of src) still runs (programmatic dependent launch).  A box that holds
+        // The kernel may start while the previous launch still runs (programmatic
+        // dependent launch).  After a ghost-face refresh of src, a box that holds
         // no ghost cell reads only interior cells, which the step before that
-        // wrote; a box touching a face waits for the previous grid first.
-        if (wait_prior && (bx == 0 || x0 + W >= g.nx || by == 0 || y0 + TY >= g.ny || zc0 == 0 || zc1 == g.nz))
+        // wrote, so only boxes touching a face wait for the previous grid; after
+        // anything else (a step that wrote its own images, the first step of a
+        // call) every box waits.
+        if ((mode & kWaitAll) ||
+            ((mode & kWaitFaces) &&
+             (bx == 0 || x0 + W >= g.nx || by == 0 || y0 + TY >= g.ny || zc0 == 0 || zc1 == g.nz)))
             asm volatile("griddepcontrol.wait;" ::: "memory");
         int issued = 0;
         bool ok = true;
@@ -488,12 +516,13 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
             if (I >= NS && !mbar_wait_sleep(&empty[s], ((I / NS) - 1) & 1)) { ok = false; break; }
             if (tmap) {
                 mbar_expect_tx(&full[s], (uint32_t)Sh::BOX_BYTES);
-                // one box: padded x from the left halo chunk (x0), padded rows y0..,
-                // padded plane zc0 + i; out-of-range parts are zero-filled, never used
-                tma_load_3d(stages + s * STAGE, tmap, x0, y0, zc0 + i, &full[s]);
+                // one box: padded x from the 16-byte chunk left of the tile (x0 + off
+                // - VX, 16-byte aligned), padded rows y0.., padded plane zc0 + i;
+                // out-of-range parts are zero-filled, never used
+                tma_load_3d(stages + s * STAGE, tmap, x0 + g.off - VX, y0, zc0 + i, &full[s]);
             } else {
                 // row by row (no tensor map): the box's rows that lie in the buffer
-                const long long row0 = (long long)x0;
+                const long long row0 = (long long)(x0 + g.off - VX);
                 const int bytes_row = (int)min((long long)SW, (long long)g.pitch - row0) * (int)sizeof(S);
                 const int nrows = min(ROWS, g.ny + 2 - y0);
                 mbar_expect_tx(&full[s], (uint32_t)(bytes_row * nrows));
@@ -520,6 +549,25 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
     const int gy = y0 + ty;
     const S *rbase = stages + (ty + 1) * SW + VX + tx * VX;   // first own row in a stage
     S *obase = dst + cell_index(g, gx, gy, 0);                // plane 0, first own row
+    // Periodic images (IMG: all faces periodic, nx a multiple of 2 VX, nx >= 4 VX,
+    // ny >= 2): a cell in the first two 16-byte chunks of a row also goes to the
+    // sector right of the row (x + nx), one in the last two chunks to the sector
+    // left of it (x - nx); the two threads of a sector store it in one request.
+    // Rows 0 and ny - 1 also go to the ghost rows across (y -+ ny), with the x
+    // image.  These offsets (elements) are 0 where a cell has no image.
+    int ximg = 0, yimg[RPT];
+    bool img = false;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) yimg[r] = 0;
+    if constexpr (IMG) {
+        ximg = gx < 2 * VX ? g.nx : (gx >= g.nx - 2 * VX ? -g.nx : 0);
+        img = ximg != 0;
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            yimg[r] = gy + r == 0 ? g.ny * g.pitch : (gy + r == g.ny - 1 ? -g.ny * g.pitch : 0);
+            img = img || yimg[r] != 0;
+        }
+    }
 
     bool ok = true;
     auto body = [&](int i, PlaneQ<T, NP> (&m)[RPT], PlaneQ<T, NP> (&z)[RPT],
@@ -693,6 +741,13 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
                 S *optr = obase + (long long)oz * g.plane + (long long)r * g.pitch;
                 if (gx + VX <= g.nx) {
                     Io<S, T>::st(optr, outv);
+                    if (IMG && img) {
+                        if (ximg) Io<S, T>::st(optr + ximg, outv);
+                        if (yimg[r]) {
+                            Io<S, T>::st(optr + yimg[r], outv);
+                            if (ximg) Io<S, T>::st(optr + yimg[r] + ximg, outv);
+                        }
+                    }
                 } else {
 #pragma unroll
                     for (int e = 0; e < VX; ++e)
@@ -709,19 +764,38 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
         if (!body(i + 1, q2, q0, q1)) break;
         if (!body(i + 2, q0, q1, q2)) break;
     }
+    // Images across the z faces, after the march so that the plane loop stays
+    // free of them: the threads of a tile holding plane 0 or nz - 1 read back
+    // their own stores of that plane (program order) and copy them.
+    if (IMG && ok && gx < g.nx && (zc0 == 0 || zc1 == g.nz)) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int oz = e == 0 ? 0 : g.nz - 1;
+            if (oz < zc0 || oz >= zc1 || (e == 1 && oz == 0)) continue;
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) {
+                if (gy + r >= g.ny) continue;
+                const uint4 v = *reinterpret_cast<const uint4 *>(dst + cell_index(g, gx, gy + r, oz));
+                store_z_images<S>(g, dst, gx, gy + r, oz, v, ximg, yimg[r]);
+            }
+        }
+    }
     return ok;
 }
 
 // minimum resident CTAs per SM (two 288-thread CTAs leave 113 registers a thread)
 template <class S> struct MinBlocks { static constexpr int value = SPFM_MIN_CTAS; };
 
-template <class S, class T, int STENCIL, int KIND, int TX, int TY, int RPT_>
+template <class S, class T, int STENCIL, int KIND, int TX, int TY, int RPT_, bool IMG>
 __global__ void __launch_bounds__(TileShape<S, T, TX, TY, RPT_>::NTHREADS, RPT_ == 1 ? 2 : MinBlocks<S>::value)
     spfm_step_kernel(const StepCoef<T> C, const PackCoef<T> PC, const S *__restrict__ src,
                      S *__restrict__ dst, int *__restrict__ err, int zchunk,
-                     const __grid_constant__ CUtensorMap tmap, int use_tmap, int pdl)
+                     const __grid_constant__ CUtensorMap tmap, int use_tmap, int mode)
 {
     using Sh = TileShape<S, T, TX, TY, RPT_>;
+    // a step that writes its own ghost images lets the next step launch at once:
+    // every box of that step waits for this grid (kWaitAll) before it reads
+    if constexpr (IMG) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     __shared__ __align__(128) S stages[Sh::NS * Sh::STAGE];
     __shared__ __align__(8) uint64_t full[Sh::NS], empty[Sh::NS];
     if (threadIdx.x == 0) {
@@ -734,9 +808,9 @@ __global__ void __launch_bounds__(TileShape<S, T, TX, TY, RPT_>::NTHREADS, RPT_ 
     __syncthreads();
     const int zc0 = blockIdx.z * zchunk;
     const int zc1 = min(zc0 + zchunk, C.g.nz);
-    step_tile<S, T, STENCIL, KIND, TX, TY, RPT_>(C, PC, src, dst, err, use_tmap ? &tmap : nullptr,
+    step_tile<S, T, STENCIL, KIND, TX, TY, RPT_, IMG>(C, PC, src, dst, err, use_tmap ? &tmap : nullptr,
                                                  blockIdx.x, blockIdx.y, zc0, zc1, stages, full, empty, 0,
-                                                 true, pdl != 0);
+                                                 true, mode);
 }
 
 // ------------------------------------------------------------------- batches
@@ -830,10 +904,10 @@ cudaError_t launch_batch_t(const void *grids, const BatchItem *work, int nwork, 
     return cudaGetLastError();
 }
 
-// z-chunk length so that the launch has enough CTAs for 152 SMs
-inline int pick_zchunk(int tiles_xy, int nz)
+// z-chunk length so that the launch has about `target` CTAs (chunks of 16
+// planes or more)
+inline int pick_zchunk(int tiles_xy, int nz, int target)
 {
-    const int target = 2048;
     int chunks = (target + tiles_xy - 1) / tiles_xy;
     int max_chunks = nz / 16 > 1 ? nz / 16 : 1;
     if (chunks > max_chunks) chunks = max_chunks;
@@ -841,13 +915,19 @@ inline int pick_zchunk(int tiles_xy, int nz)
     return (nz + chunks - 1) / chunks;
 }
 
-template <class S, class T, int TX, int TY>
+// IMG: the kernels that write the periodic ghost images (cfg.mode has kImages)
+template <class S, class T, int TX, int TY, bool IMG>
 cudaError_t launch_step_t(const StepCoef<T> &c, const S *src, S *dst, int *err, LaunchCfg cfg,
                           const CUtensorMap *tmap, cudaStream_t st)
 {
     using Sh = TileShape<S, T, TX, TY>;
     const int gxn = (c.g.nx + Sh::W - 1) / Sh::W, gyn = (c.g.ny + TY - 1) / TY;
-    const int zchunk = pick_zchunk(gxn * gyn, c.g.nz);
+    // about six waves of three resident CTAs per SM: fewer, longer CTAs leave a
+    // longer tail, shorter ones re-read more halo planes (512^3 FP32 sweep)
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int zchunk = pick_zchunk(gxn * gyn, c.g.nz, 6 * 3 * sms);
     const dim3 grid(gxn, gyn, (c.g.nz + zchunk - 1) / zchunk);
     // exact group counts 1..4 get their own kernels; 0 groups (all A_k = 0)
     // runs the one-group kernel with beta = 0
@@ -862,7 +942,7 @@ cudaError_t launch_step_t(const StepCoef<T> &c, const S *src, S *dst, int *err, 
     constexpr int R = SPFM_ROWS_PER_THREAD;
     constexpr int NT1 = TileShape<S, T, TX, TY, 1>::NTHREADS;
     // programmatic dependent launch: the kernel may begin while the previous
-    // kernel in the stream runs; boxes touching a face wait (griddepcontrol)
+    // kernel in the stream runs; cfg.mode says which boxes wait (griddepcontrol)
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
@@ -872,13 +952,13 @@ cudaError_t launch_step_t(const StepCoef<T> &c, const S *src, S *dst, int *err, 
     lc.stream = st;
     lc.attrs = attr;
     lc.numAttrs = 1;
-    const int pdl = 1;
+    const int mode = cfg.mode;
     auto go = [&](auto kern, int threads) {
         lc.blockDim = dim3(threads);
-        return cudaLaunchKernelEx(&lc, kern, c, pc, src, dst, err, zchunk, map, use, pdl);
+        return cudaLaunchKernelEx(&lc, kern, c, pc, src, dst, err, zchunk, map, use, mode);
     };
     cudaError_t le = cudaSuccess;
-#define SPFM_LAUNCH(ST, KD) le = go(spfm_step_kernel<S, T, ST, KD, TX, TY, R>, Sh::NTHREADS)
+#define SPFM_LAUNCH(ST, KD) le = go(spfm_step_kernel<S, T, ST, KD, TX, TY, R, IMG>, Sh::NTHREADS)
 #define SPFM_BY_KIND(ST)                        \
     do {                                        \
         if (kind == 0) SPFM_LAUNCH(ST, 0);      \
@@ -887,7 +967,7 @@ cudaError_t launch_step_t(const StepCoef<T> &c, const S *src, S *dst, int *err, 
         else if (kind == 3) SPFM_LAUNCH(ST, 3); \
         else if (kind == 4) SPFM_LAUNCH(ST, 4); \
         else if (kind == 5) SPFM_LAUNCH(ST, 5); \
-        else le = go(spfm_step_kernel<S, T, ST, 6, TX, TY, 1>, NT1); \
+        else le = go(spfm_step_kernel<S, T, ST, 6, TX, TY, 1, IMG>, NT1); \
     } while (0)
     if (cfg.stencil == 6) SPFM_BY_KIND(6);
     else if (cfg.stencil == 18) SPFM_BY_KIND(18);

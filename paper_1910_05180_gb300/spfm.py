@@ -99,6 +99,7 @@ SIGNATURES = [
     ("spfm_get_field", _I, [_P, _P, _I]),
     ("spfm_set_field", _I, [_P, _P, _I]),
     ("spfm_current", _I, [_P]),
+    ("spfm_kernels_per_step", _I, [_P]),
     ("spfm_last_error", ctypes.c_char_p, [_P]),
     ("spfm_batch_scratch_bytes", _I, [ctypes.POINTER(_P), _I, ctypes.POINTER(ctypes.c_size_t)]),
     ("spfm_batch_create", _I, [ctypes.POINTER(_P), _I, _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
@@ -229,6 +230,10 @@ def spfm_current(h) -> int:
     return load().spfm_current(h)
 
 
+def spfm_kernels_per_step(h) -> int:
+    return load().spfm_kernels_per_step(h)
+
+
 def spfm_last_error(h=None) -> str:
     m = load().spfm_last_error(h)
     return m.decode() if m else ""
@@ -310,6 +315,10 @@ class Grid:
 
     def sphericity(self, inside_phase=0) -> dict:
         return spfm_sphericity(self.handle, inside_phase)
+
+    def kernels_per_step(self) -> int:
+        """1 when the step kernel writes the periodic ghost images itself, else 2."""
+        return spfm_kernels_per_step(self.handle)
 
     def current(self) -> torch.Tensor:
         """View (nz, ny, nx) of the interior of the buffer holding the current field."""

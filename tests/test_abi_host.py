@@ -53,11 +53,11 @@ def _desc(nx=10, ny=7, nz=5, dtype=S.SPFM_F32, bc=(S.SPFM_PERIODIC,) * 6, n=(1.0
     return d
 
 
-@pytest.mark.parametrize("dtype,per16", [(S.SPFM_F64, 2), (S.SPFM_F32, 4), (S.SPFM_BF16, 8)])
-def test_layout_pitch_is_16_byte_rows(lib, dtype, per16):
+@pytest.mark.parametrize("dtype,per32", [(S.SPFM_F64, 4), (S.SPFM_F32, 8), (S.SPFM_BF16, 16)])
+def test_layout_rows_are_whole_32_byte_sectors(lib, dtype, per32):
     for nx in (1, 3, 4, 17, 128, 130):
         px, xo, fb, sb = S.spfm_layout(_desc(nx=nx, dtype=dtype))
-        assert xo == per16 and px % per16 == 0 and xo + nx + 1 <= px < xo + nx + 1 + per16
+        assert xo == per32 and px % per32 == 0 and xo + nx + 1 <= px < xo + nx + 1 + per32
         es = {S.SPFM_F64: 8, S.SPFM_F32: 4, S.SPFM_BF16: 2}[dtype]
         assert fb == px * (7 + 2) * (5 + 2) * es
         assert sb > 0
@@ -70,6 +70,34 @@ def _fake_grid(lib, **kw):
     d.field[0], d.field[1] = 0x10000, 0x20000
     d.scratch, d.scratch_bytes = 0x30000, sb
     return S.spfm_create_grid(d)
+
+
+def test_kernels_per_step_follows_the_periodic_image_rule(lib):
+    """One launch per step (the step writes its own periodic ghost images) only
+    with every face periodic, nx a whole number (>= 2) of 32-byte sectors and
+    ny >= 2; otherwise the ghost-face kernel follows each step."""
+    P, C = (S.SPFM_PERIODIC,) * 6, (S.SPFM_CONTACT,) * 6
+    mixed = (S.SPFM_PERIODIC,) * 4 + (S.SPFM_NOFLUX,) * 2
+    cases = [
+        (dict(nx=16, ny=2, nz=1, dtype=S.SPFM_F32, bc=P), 1),
+        (dict(nx=512, ny=512, nz=512, dtype=S.SPFM_F32, bc=P), 1),
+        (dict(nx=8, ny=5, nz=5, dtype=S.SPFM_F32, bc=P), 2),      # one sector only
+        (dict(nx=20, ny=5, nz=5, dtype=S.SPFM_F32, bc=P), 2),     # not whole sectors
+        (dict(nx=16, ny=1, nz=5, dtype=S.SPFM_F32, bc=P), 2),     # ny = 1
+        (dict(nx=16, ny=5, nz=5, dtype=S.SPFM_F32, bc=C), 2),
+        (dict(nx=16, ny=5, nz=5, dtype=S.SPFM_F32, bc=mixed), 2),
+        (dict(nx=8, ny=5, nz=5, dtype=S.SPFM_F64, bc=P), 1),
+        (dict(nx=4, ny=5, nz=5, dtype=S.SPFM_F64, bc=P), 2),
+        (dict(nx=32, ny=5, nz=5, dtype=S.SPFM_BF16, bc=P), 1),
+        (dict(nx=16, ny=5, nz=5, dtype=S.SPFM_BF16, bc=P), 2),
+    ]
+    for kw, want in cases:
+        h = _fake_grid(lib, **kw)
+        try:
+            assert S.spfm_kernels_per_step(h) == want, kw
+        finally:
+            S.spfm_destroy_grid(h)
+    assert S.spfm_kernels_per_step(None) == -1
 
 
 def test_create_grid_validation(lib):

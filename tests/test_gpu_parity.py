@@ -86,6 +86,13 @@ CASES = [
     ((130, 2, 3), (S.SPFM_PERIODIC,) * 2 + (S.SPFM_CONTACT,) * 4, 26, S.SPFM_TI_LOCAL),
     ((65, 17, 33), (S.SPFM_CONTACT,) * 6, 26, S.SPFM_FD_HABEL),
     ((64, 16, 32), (S.SPFM_CONTACT,) * 6, 26, S.SPFM_FD_H5),
+    # all faces periodic with rows of whole 32-byte sectors (nx a multiple of 8
+    # FP32 / 4 FP64 cells): the step writes its own ghost images
+    ((64, 18, 35), (S.SPFM_PERIODIC,) * 6, 26, S.SPFM_TI_GLOBAL),
+    ((8, 1, 1), (S.SPFM_PERIODIC,) * 6, 26, S.SPFM_FD),
+    ((136, 3, 1), (S.SPFM_PERIODIC,) * 6, 18, S.SPFM_TI_LOCAL),
+    ((4, 5, 6), (S.SPFM_PERIODIC,) * 6, 26, S.SPFM_TI_GLOBAL),   # images in FP64 only
+    ((16, 1, 7), (S.SPFM_PERIODIC,) * 6, 6, S.SPFM_FD_H5),
 ]
 
 
@@ -123,6 +130,85 @@ def test_step_count_and_ping_pong_agree():
     for _ in range(7):
         g2.step(1, lam=3.0, dt=0.05, dF=0.02)
     assert torch.equal(g1.get_field(), g2.get_field())
+
+
+# ------------------------------------------------ periodic ghost images
+
+
+@pytest.mark.parametrize("dtype", [S.SPFM_F64, S.SPFM_F32, S.SPFM_BF16])
+@pytest.mark.parametrize("shape", [(32, 1, 1), (48, 5, 1), (144, 33, 3), (20, 3, 2)])
+def test_periodic_ghost_layer_is_the_exact_wrap(dtype, shape):
+    """All faces periodic: after every step the ghost layer (edges and corners
+    included) holds the periodic wrap of the interior, value for value, both
+    where the step kernel writes the images itself (nx a whole number of
+    32-byte sectors) and where the face kernel does (nx = 20 in FP32 / BF16)."""
+    nx, ny, nz = shape
+    n = rng_normal(41)
+    g, p = make_pair(nx, ny, nz, dtype, (S.SPFM_PERIODIC,) * 6, n, lam=2.5)
+    rng = np.random.default_rng(42)
+    phi0 = O.init_planar(p, float(n @ (np.array(shape) - 1) / 2.0)) + 0.01 * rng.random(p.shape)
+    upload(g, phi0, dtype)
+    for steps in (1, 2, 5):
+        g.step(steps, lam=2.5, dt=0.05, dF=0.03, stencil=26)
+        full = g.current_with_ghosts().double().cpu().numpy()
+        assert np.array_equal(full, np.pad(full[1:-1, 1:-1, 1:-1], 1, mode="wrap"))
+
+
+def test_periodic_image_steps_around_conserving_steps():
+    """Steps that write their own ghost images, then constant-volume steps
+    (face kernel after the correction), then image steps again, on one
+    periodic FP64 grid: the field stays on the oracle's."""
+    N, lam = 32, 2.5
+    u = tuple(np.array([1.0, 2.0, 0.0]) / np.sqrt(5.0))
+    g, p = make_pair(N, N, N, S.SPFM_F64, (S.SPFM_PERIODIC,) * 6, u, lam=lam, dt=0.05, dF=0.04)
+    p0 = O.Params(N, N, N, bc=(O.PERIODIC,) * 6, n=u, lam=lam, dt=0.05, stencil=26, scheme=O.TI_GLOBAL)
+    start = upload(g, O.init_cube(p, ((N - 1) / 2.0,) * 3, 8.0), S.SPFM_F64)
+    g.step(5, lam=lam, dt=0.05, dF=0.04)
+    g.step_conserving(5, lam=lam, dt=0.05)
+    g.step(5, lam=lam, dt=0.05, dF=0.04)
+    ref = O.step(p, start, 5)
+    ref, _ = O.step_conserving(p0, ref, 5)
+    ref = O.step(p, ref, 5)
+    assert np.abs(gpu_field(g) - ref).max() <= 1e-12
+
+
+def wrapped_cone_reference(phi_start, sample, T, p_kwargs):
+    """Value of one cell of an all-periodic grid after T steps, from an oracle
+    run on the (2T+1)^3 box of its dependency cone, indices wrapped."""
+    nz, ny, nx = phi_start.shape
+    k, j, i = sample
+    idx = [np.arange(c - T, c + T + 1) % n for c, n in ((k, nz), (j, ny), (i, nx))]
+    sub = np.ascontiguousarray(phi_start[np.ix_(*idx)])
+    w = 2 * T + 1
+    p = O.Params(w, w, w, bc=(O.NOFLUX,) * 6, **p_kwargs)
+    return O.step(p, sub, T)[T, T, T]
+
+
+def test_grain_512cubed_sampled_cone_parity():
+    """The benchmark's grain in its launch configuration: 512^3 FP32, R = 150,
+    TI_<120>, 27-point, all faces periodic (the step writes its own ghost
+    images), 4 steps; 72 sampled cells (corners, edges, faces, across the
+    interface, random) against oracle runs on their wrapped dependency cones."""
+    w = WL.sphere_512cubed()
+    N, T = w["nx"], 4
+    g = S.Grid(N, N, N, dtype=S.SPFM_F32, bc=(S.SPFM_PERIODIC,) * 6, n=w["u"], center=w["ctr"])
+    p = O.Params(N, N, N, bc=(O.PERIODIC,) * 6, n=w["u"], lam=w["lam"])
+    start = upload(g, O.init_sphere(p, w["ctr"], w["R"]), S.SPFM_F32)
+    g.step(T, lam=w["lam"], dt=w["dt"], dF=w["dF"], stencil=26)
+    out = g.current().double().cpu().numpy()
+    rng = np.random.default_rng(7)
+    pts = [(z, y, x) for z in (0, N - 1) for y in (0, N - 1) for x in (0, N - 1)]
+    pts += [(0, int(a), N - 1) for a in rng.integers(0, N, 8)]                 # edges
+    pts += [(int(a), int(b), 0) for a, b in rng.integers(0, N, (8, 2))]        # faces
+    pts += [(N - 1, int(a), int(b)) for a, b in rng.integers(0, N, (8, 2))]
+    for d in rng.normal(size=(24, 3)):                                        # the interface
+        q = np.array(w["ctr"]) + (w["R"] + rng.uniform(-3, 3)) * d / np.linalg.norm(d)
+        pts.append(tuple(int(round(v)) % N for v in q[::-1]))
+    pts += [tuple(int(v) for v in rng.integers(0, N, 3)) for _ in range(16)]
+    kw = dict(n=w["u"], lam=w["lam"], dt=w["dt"], dF=w["dF"], stencil=26, scheme=O.TI_GLOBAL)
+    errs = [abs(out[s] - wrapped_cone_reference(start, s, T, kw)) for s in pts]
+    assert max(errs) <= TOL[S.SPFM_F32], max(errs)
+    assert sum(1e-6 < out[s] < 1 - 1e-6 for s in pts) >= 16    # the samples do cross the band
 
 
 # ---------------------------------------------------------------- stats
