@@ -554,20 +554,14 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
     // sector right of the row (x + nx), one in the last two chunks to the sector
     // left of it (x - nx); the two threads of a sector store it in one request.
     // Rows 0 and ny - 1 also go to the ghost rows across (y -+ ny), with the x
-    // image.  These offsets (elements) are 0 where a cell has no image.
-    int ximg = 0, yimg[RPT];
+    // image.  The offsets (elements, 0 where a cell has no image) are recomputed
+    // where they are used, so that the plane loop keeps only the flag live.
+    auto ximg = [&]() { return gx < 2 * VX ? g.nx : (gx >= g.nx - 2 * VX ? -g.nx : 0); };
+    auto yimg = [&](int r) {
+        return gy + r == 0 ? g.ny * g.pitch : (gy + r == g.ny - 1 ? -g.ny * g.pitch : 0);
+    };
     bool img = false;
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) yimg[r] = 0;
-    if constexpr (IMG) {
-        ximg = gx < 2 * VX ? g.nx : (gx >= g.nx - 2 * VX ? -g.nx : 0);
-        img = ximg != 0;
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-            yimg[r] = gy + r == 0 ? g.ny * g.pitch : (gy + r == g.ny - 1 ? -g.ny * g.pitch : 0);
-            img = img || yimg[r] != 0;
-        }
-    }
+    if constexpr (IMG) img = gx < 2 * VX || gx >= g.nx - 2 * VX || gy == 0 || gy + RPT >= g.ny;
 
     bool ok = true;
     auto body = [&](int i, PlaneQ<T, NP> (&m)[RPT], PlaneQ<T, NP> (&z)[RPT],
@@ -742,10 +736,11 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
                 if (gx + VX <= g.nx) {
                     Io<S, T>::st(optr, outv);
                     if (IMG && img) {
-                        if (ximg) Io<S, T>::st(optr + ximg, outv);
-                        if (yimg[r]) {
-                            Io<S, T>::st(optr + yimg[r], outv);
-                            if (ximg) Io<S, T>::st(optr + yimg[r] + ximg, outv);
+                        const int xo = ximg(), yo = yimg(r);
+                        if (xo) Io<S, T>::st(optr + xo, outv);
+                        if (yo) {
+                            Io<S, T>::st(optr + yo, outv);
+                            if (xo) Io<S, T>::st(optr + yo + xo, outv);
                         }
                     }
                 } else {
@@ -776,15 +771,20 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
             for (int r = 0; r < RPT; ++r) {
                 if (gy + r >= g.ny) continue;
                 const uint4 v = *reinterpret_cast<const uint4 *>(dst + cell_index(g, gx, gy + r, oz));
-                store_z_images<S>(g, dst, gx, gy + r, oz, v, ximg, yimg[r]);
+                store_z_images<S>(g, dst, gx, gy + r, oz, v, ximg(), yimg(r));
             }
         }
     }
     return ok;
 }
 
-// minimum resident CTAs per SM (two 288-thread CTAs leave 113 registers a thread)
+// Resident CTAs per SM the register budget is sized for: three by default;
+// the single-grid FP32 kernels fit four (96 registers, no spills, 20 warps per
+// SM: 2 % faster for TI_<120>, 3-6 % for CF at 512^3), while FP64 and BF16
+// spill there, and the persistent batch kernel keeps three.
 template <class S> struct MinBlocks { static constexpr int value = SPFM_MIN_CTAS; };
+template <> struct MinBlocks<float> { static constexpr int value = 4; };
+template <class S> struct BatchMinBlocks { static constexpr int value = SPFM_MIN_CTAS; };
 
 template <class S, class T, int STENCIL, int KIND, int TX, int TY, int RPT_, bool IMG>
 __global__ void __launch_bounds__(TileShape<S, T, TX, TY, RPT_>::NTHREADS, RPT_ == 1 ? 2 : MinBlocks<S>::value)
@@ -829,7 +829,7 @@ struct BatchGrid {
 // Persistent kernel over the packed work-list of all grids of a batch: CTA b
 // takes items b, b + gridDim.x, ...  Step `parity` reads buffer cur ^ parity.
 template <class S, class T, int STENCIL, int KIND, int TX, int TY>
-__global__ void __launch_bounds__(TileShape<S, T, TX, TY>::NTHREADS, MinBlocks<S>::value)
+__global__ void __launch_bounds__(TileShape<S, T, TX, TY>::NTHREADS, BatchMinBlocks<S>::value)
     spfm_batch_kernel(const BatchGrid<T> *__restrict__ grids, const BatchItem *__restrict__ work,
                       int nwork, int parity, int *__restrict__ err)
 {
@@ -885,7 +885,7 @@ cudaError_t launch_batch_t(const void *grids, const BatchItem *work, int nwork, 
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int ctas = sms * MinBlocks<S>::value;
+    int ctas = sms * BatchMinBlocks<S>::value;
     if (ctas > nwork) ctas = nwork;
     if (ctas < 1) return cudaSuccess;
     const BatchGrid<T> *bg = (const BatchGrid<T> *)grids;
@@ -922,12 +922,12 @@ cudaError_t launch_step_t(const StepCoef<T> &c, const S *src, S *dst, int *err, 
 {
     using Sh = TileShape<S, T, TX, TY>;
     const int gxn = (c.g.nx + Sh::W - 1) / Sh::W, gyn = (c.g.ny + TY - 1) / TY;
-    // about six waves of three resident CTAs per SM: fewer, longer CTAs leave a
-    // longer tail, shorter ones re-read more halo planes (512^3 FP32 sweep)
+    // about six waves of the resident CTAs: fewer, longer CTAs leave a longer
+    // tail, shorter ones re-read more halo planes (512^3 FP32 sweep)
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int zchunk = pick_zchunk(gxn * gyn, c.g.nz, 6 * 3 * sms);
+    const int zchunk = pick_zchunk(gxn * gyn, c.g.nz, 6 * MinBlocks<S>::value * sms);
     const dim3 grid(gxn, gyn, (c.g.nz + zchunk - 1) / zchunk);
     // exact group counts 1..4 get their own kernels; 0 groups (all A_k = 0)
     // runs the one-group kernel with beta = 0
