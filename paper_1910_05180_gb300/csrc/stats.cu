@@ -5,8 +5,9 @@
 // profiles (the start of the Sec. 3.3 shape relaxation), evaluated in FP64 per cell and
 // rounded once to the storage type (the caller then fills the ghost layer).
 //
-// stats: one pass over the interior with FP64 sums, per lane in a fixed
-// order, then warp-shuffle and shared-memory block reductions into
+// stats: one pass over the interior with sums per lane in a fixed order
+// (double-float pairs for the band sums, FP64 otherwise, see below), then
+// FP64 warp-shuffle and shared-memory block reductions into
 // kStatsBlocks partials, then one CTA reducing the partials in a fixed order,
 // so the result is bit-reproducible for a given grid size.  Sums over the band
 // 1e-6 < phi < 1 - 1e-6 invert the ideal profile (Sec. 2.3):
@@ -225,49 +226,116 @@ template <> struct VolSum<double> {
     __device__ __forceinline__ double total() const { return sum; }
 };
 
-// (ln F_j, 1 / F_j) for F_j = 1 + j/256
-__device__ double2 g_ln_table[256];
+// ---- double-float arithmetic: a value is hi + lo in two FP32 numbers with
+// |lo| <= ulp(hi)/2 (Dekker, Numer. Math. 18, 1971; Knuth, TAOCP 2, 4.2.2).
+// About 48 significant bits at the FP32 rate, 64 times the FP64 rate of this
+// GPU.  The error-free transforms use the _rn intrinsics, which the compiler
+// neither contracts into FMAs nor reassociates.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF df_two_sum(float a, float b)   // a + b exactly
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DF df_fast_sum(float a, float b)  // a + b exactly, |a| >= |b| or a = 0
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_two_prod(float a, float b)  // a b exactly
+{
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+// a + b with absolute error about 2^-48 max(|a|, |b|)
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    const DF s = df_two_sum(a.hi, b.hi);
+    return df_fast_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+// a + b with the low parts also added error-free, for running sums
+__device__ __forceinline__ DF df_add_acc(DF a, DF b)
+{
+    DF s = df_two_sum(a.hi, b.hi);
+    const DF t = df_two_sum(a.lo, b.lo);
+    s = df_fast_sum(s.hi, __fadd_rn(s.lo, t.hi));
+    return df_fast_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ DF df_neg(DF a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ DF df_mul(DF a, DF b)
+{
+    const DF p = df_two_prod(a.hi, b.hi);
+    return df_fast_sum(p.hi, __fadd_rn(p.lo, __fmaf_rn(a.hi, b.lo, __fmul_rn(a.lo, b.hi))));
+}
+__device__ __forceinline__ DF df_mul_f(DF a, float b)
+{
+    const DF p = df_two_prod(a.hi, b);
+    return df_fast_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
+}
+__host__ __device__ __forceinline__ DF df_of(double x)
+{
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
+// sqrt of a non-negative value: the FP32 root s and one Newton step,
+// s + (a - s^2) / (2 s), with s^2 formed exactly
+__device__ __forceinline__ DF df_sqrt(DF a)
+{
+    if (!(a.hi > 0.0f)) return {0.0f, 0.0f};
+    const float s = sqrtf(a.hi);
+    const DF s2 = df_two_prod(s, s);
+    const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, s2.hi), s2.lo), a.lo);
+    return df_fast_sum(s, __fmul_rn(r, __fdiv_rn(0.5f, s)));
+}
+
+// Tables of the band evaluation, as double-float pairs written from FP64:
+// g_ln_tab[j] = (ln F_j, 1/F_j) for F_j = 1 + j/256, g_kln2[k + 64] = k ln 2.
+__device__ float4 g_ln_tab[256];
+__device__ float2 g_kln2[128];
 
 __global__ void ln_table_kernel()
 {
-    const double F = 1.0 + threadIdx.x / 256.0;
-    g_ln_table[threadIdx.x] = make_double2(log(F), 1.0 / F);
+    const int j = threadIdx.x;
+    const double F = 1.0 + j / 256.0;
+    const DF l = df_of(log(F)), r = df_of(1.0 / F);
+    g_ln_tab[j] = make_float4(l.hi, l.lo, r.hi, r.lo);
+    if (j < 128) {
+        const DF k = df_of((double)(j - 64) * 0.69314718055994530942);
+        g_kln2[j] = make_float2(k.hi, k.lo);
+    }
 }
 
-// ln y for a normal y in (0, 1], table-driven (Tang, ACM TOMS 16, 1990):
-// y = 2^k m, m in [1, 2); F = 1 + j/256 takes the top 8 fraction bits of m, so
-// f = m - F is exact and u = f/F lies in [0, 2^-8).  ln(1 + u) is its Taylor
-// series: u - u^2/2 in FP64, the terms u^3/3 - u^4/4 + u^5/5 (below 2e-8) in
-// FP32, truncation below u^6/6 < 6e-16.  Returned as k, ln F and ln(1 + u).
+// ln y for y = hi + lo in [2^-126, 1], table-driven (Tang, ACM TOMS 16, 1990):
+// hi = 2^k m, m in [1, 2); F = 1 + j/256 takes the top 8 fraction bits of m, so
+// f = (m - F) + lo 2^-k holds y 2^-k - F to double-float accuracy and u = f/F
+// lies in (-2^-24, 2^-8).  ln(1 + u) is its Taylor series: u - u^2/2 in
+// double-float, the terms u^3/3 - u^4/4 + u^5/5 (below 2e-8) in FP32,
+// truncation below u^6/6 < 6e-16.  Returned as k, ln F and ln(1 + u).
 struct LnParts {
     int k;
-    double lnF, s;
+    DF lnF, s;
 };
-__device__ __forceinline__ LnParts ln_parts(double y, const double2 *tab)
+__device__ __forceinline__ LnParts ln_parts(DF y, const float4 *tab)
 {
-    const int hi = __double2hiint(y), lo = __double2loint(y);
-    const int j = (hi >> 12) & 0xff;
-    const double m = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, lo);
-    const double F = __hiloint2double(0x3ff00000 | (j << 12), 0);
-    const double2 t = tab[j];
-    const double u = (m - F) * t.y;
-    const float uf = (float)u;
-    const float tail = uf * uf * uf * fmaf(uf, fmaf(uf, 0.2f, -0.25f), 1.0f / 3.0f);
+    const int bits = __float_as_int(y.hi);
     LnParts r;
-    r.k = ((hi >> 20) & 0x7ff) - 1023;
-    r.lnF = t.x;
-    r.s = fma(-0.5 * u, u, u) + (double)tail;
+    r.k = ((bits >> 23) & 0xff) - 127;
+    const int j = (bits >> 15) & 0xff;
+    const float m = __int_as_float((bits & 0x007fffff) | 0x3f800000);
+    const float F = __int_as_float(0x3f800000 | (j << 15));
+    const float lo = __fmul_rn(y.lo, __int_as_float((127 - r.k) << 23));   // lo 2^-k, exact
+    const float4 t = tab[j];
+    r.lnF = {t.x, t.y};
+    const DF u = df_mul(df_two_sum(__fsub_rn(m, F), lo), DF{t.z, t.w});
+    const DF u2 = df_mul(u, u);
+    const float uh = u.hi;
+    const float tail = uh * uh * uh * fmaf(uh, fmaf(uh, 0.2f, -0.25f), 1.0f / 3.0f);
+    r.s = df_add(df_add(u, DF{-0.5f * u2.hi, -0.5f * u2.lo}), DF{tail, 0.0f});
     return r;
-}
-
-// sqrt(r2) in FP64 from the FP32 square root and one Newton step in FP64
-// (relative error below 2e-14); 0, tiny, huge and non-finite r2 take sqrt
-__device__ __forceinline__ double dist_from_r2(double r2)
-{
-    const float rf = sqrtf((float)r2);
-    if (!(rf > 1e-15f && rf < 1e15f)) return sqrt(r2);
-    const double r0 = (double)rf;
-    return fma(fma(-r0, r0, r2), (double)(0.5f / rf), r0);
 }
 
 // one band cell waiting in its warp's queue: value, x index, and its row's
@@ -275,30 +343,52 @@ __device__ __forceinline__ double dist_from_r2(double r2)
 template <class R> struct BandCell {
     R phi;
     int i;
-    double pn_row, ryz2;
+    DF pn_row, ryz2;
 };
 
-// Sec. 2.3 sums of one band cell: q = phi(1 - phi), psi = (lambda/2) artanh(1 - 2 phi)
-// = (lambda/4) (ln(1 - phi) - ln phi), p = dx (i, j, k)
+// Sec. 2.3 sums of one band cell, in double-float: q = phi(1 - phi),
+// psi = (lambda/2) artanh(1 - 2 phi) = (lambda/4) (ln(1 - phi) - ln phi),
+// p = dx (i, j, k).  Absolute error of psi below about 1e-13.
 struct BandConst {
-    double dxn0, dx, c0, quarter_lambda;
+    DF dxn0, dx, neg_c0, quarter_lambda;
+};
+template <class R> struct BandPhi;
+template <> struct BandPhi<float> {   // FP32 and BF16 storage: phi exact, 1 - phi exact as a pair
+    static __device__ __forceinline__ void get(float x, DF &ph, DF &om)
+    {
+        ph = {x, 0.0f};
+        om = df_fast_sum(1.0f, -x);
+    }
+};
+template <> struct BandPhi<double> {  // FP64 storage: 1 - phi in FP64, then both as pairs
+    static __device__ __forceinline__ void get(double x, DF &ph, DF &om)
+    {
+        ph = df_of(x);
+        om = df_of(1.0 - x);
+    }
+};
+struct BandSums {
+    DF w{0.0f, 0.0f}, c{0.0f, 0.0f}, r{0.0f, 0.0f};   // S_w, S_c, S_r
 };
 template <class R>
-__device__ __forceinline__ void band_cell(const BandConst &bc, const BandCell<R> &c, const double2 *tab, double *v)
+__device__ __forceinline__ void band_cell(const BandConst &bc, const BandCell<R> &c, const float4 *tab,
+                                          const float2 *kln2, BandSums &acc)
 {
-    const double ph = (double)c.phi;
-    const double om = 1.0 - ph;   // exact
-    const double q = ph * om;
+    DF ph, om;
+    BandPhi<R>::get(c.phi, ph, om);
+    const DF q = df_mul(ph, om);
     const LnParts l1 = ln_parts(om, tab), l0 = ln_parts(ph, tab);
-    const double d = fma((double)(l1.k - l0.k), 0.69314718055994530942, (l1.lnF - l0.lnF) + (l1.s - l0.s));
-    const double psi = bc.quarter_lambda * d;
-    const double di = (double)c.i;
-    const double pn = fma(di, bc.dxn0, c.pn_row);
-    const double rx = fma(di, bc.dx, -bc.c0);
-    const double r = dist_from_r2(fma(rx, rx, c.ryz2));
-    v[1] += q;
-    v[2] += q * (pn - psi);
-    v[3] += q * (r + psi);
+    const float2 kl = kln2[l1.k - l0.k + 64];
+    DF d = df_add(DF{kl.x, kl.y}, df_add(l1.lnF, df_neg(l0.lnF)));
+    d = df_add(d, df_add(l1.s, df_neg(l0.s)));
+    const DF psi = df_mul(bc.quarter_lambda, d);
+    const float fi = (float)c.i;
+    const DF pn = df_add(c.pn_row, df_mul_f(bc.dxn0, fi));
+    const DF rx = df_add(df_mul_f(bc.dx, fi), bc.neg_c0);
+    const DF r = df_sqrt(df_add(df_mul(rx, rx), c.ryz2));
+    acc.w = df_add_acc(acc.w, q);
+    acc.c = df_add_acc(acc.c, df_mul(q, df_add(pn, df_neg(psi))));
+    acc.r = df_add_acc(acc.r, df_mul(q, df_add(r, psi)));
 }
 
 // Partial sums of block b of nb (256 threads): rows ordered (j fastest, k) are
@@ -313,7 +403,8 @@ __device__ __forceinline__ void stats_pass(const StatsArgs &a, const S *f, doubl
     constexpr int V = 16 / E;             // loads per lane and sweep
     constexpr int kWarps = 8;
     __shared__ BandCell<R> queue[kWarps][64];
-    const double2 *tab = g_ln_table;
+    const float4 *tab = g_ln_tab;
+    const float2 *kln2 = g_kln2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     BandCell<R> *qw = queue[warp];
     double v[kNStat];
@@ -321,13 +412,14 @@ __device__ __forceinline__ void stats_pass(const StatsArgs &a, const S *f, doubl
     for (int i = 0; i < kNStat; ++i) v[i] = 0.0;
     R mn = R(INFINITY), mx = R(-INFINITY);
     int nonfinite = 0, cnt = 0;
-    const BandConst bconst = {a.dx * a.n[0], a.dx, a.ctr[0], 0.25 * a.lambda};
+    const BandConst bconst = {df_of(a.dx * a.n[0]), df_of(a.dx), df_of(-a.ctr[0]), df_of(0.25 * a.lambda)};
+    BandSums sums;
     VolSum<R> vol;
     const long long rows = (long long)a.g.ny * a.g.nz;
     const int nvec = (a.g.nx + E - 1) / E;
     for (long long row = blk * kWarps + warp; row < rows; row += nblk * kWarps) {
         const int j = (int)(row % a.g.ny), k = (int)(row / a.g.ny);
-        double pn_row = 0.0, ryz2 = 0.0;   // the row's shares, once it has band cells
+        DF pn_row{0.0f, 0.0f}, ryz2{0.0f, 0.0f};   // the row's shares, once it has band cells
         bool row_known = false;
         const uint4 *src = (const uint4 *)(f + cell_index(a.g, 0, j, k));
         for (int v0 = 0; v0 < nvec; v0 += 32 * V) {
@@ -358,9 +450,9 @@ __device__ __forceinline__ void stats_pass(const StatsArgs &a, const S *f, doubl
             // queue this sweep's band cells, evaluating full warps of them
             if (!row_known && __any_sync(0xffffffffu, bm != 0u)) {
                 const double py = a.dx * j, pz = a.dx * k;
-                pn_row = py * a.n[1] + pz * a.n[2];
+                pn_row = df_of(py * a.n[1] + pz * a.n[2]);
                 const double ry = py - a.ctr[1], rz = pz - a.ctr[2];
-                ryz2 = ry * ry + rz * rz;
+                ryz2 = df_of(ry * ry + rz * rz);
                 row_known = true;
             }
             while (__any_sync(0xffffffffu, bm != 0u)) {
@@ -380,7 +472,7 @@ __device__ __forceinline__ void stats_pass(const StatsArgs &a, const S *f, doubl
                 cnt += __popc(m);
                 if (cnt >= 32) {
                     __syncwarp();
-                    band_cell<R>(bconst, qw[lane], tab, v);
+                    band_cell<R>(bconst, qw[lane], tab, kln2, sums);
                     __syncwarp();
                     cnt -= 32;
                     if (lane < cnt) qw[lane] = qw[lane + 32];
@@ -392,7 +484,10 @@ __device__ __forceinline__ void stats_pass(const StatsArgs &a, const S *f, doubl
     }
     v[0] = vol.total();
     __syncwarp();
-    if (lane < cnt) band_cell<R>(bconst, qw[lane], tab, v);
+    if (lane < cnt) band_cell<R>(bconst, qw[lane], tab, kln2, sums);
+    v[1] = df_to_double(sums.w);
+    v[2] = df_to_double(sums.c);
+    v[3] = df_to_double(sums.r);
     v[4] = (double)mn;
     v[5] = (double)mx;
     v[6] = (double)nonfinite;
@@ -496,7 +591,8 @@ static cudaError_t ensure_ln_table(cudaStream_t st)
 }
 
 // One full wave of stats blocks on this device (at most kStatsBlocks): the
-// pass is bound by the FP64 pipe, so a partial second wave would idle SMs.
+// band cells sit in a few planes and are spread over all warps, so a partial
+// second wave would idle SMs.
 template <class S> static int stats_blocks()
 {
     static int cached[128];
