@@ -172,9 +172,13 @@ template <> struct Row16<double> {
     }
 };
 
+// 1e-6 < x < 1 - 1e-6 for an FP32 x: the limits are not FP32 numbers, so the
+// test compares with the first float above 1e-6 and the last float below
+// 1 - 1e-6 (written out: a rounding conversion here would run on the FP64 pipe
+// for every cell)
 __device__ __forceinline__ bool in_band(float x)
 {
-    return x >= __double2float_ru(1e-6) && x <= __double2float_rd(1.0 - 1e-6);
+    return x >= 0x1.0c6f7cp-20f && x <= 0x1.ffffdep-1f;
 }
 __device__ __forceinline__ bool in_band(double x) { return x > 1e-6 && x < 1.0 - 1e-6; }
 

@@ -8,6 +8,7 @@ import math
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_1910_05180_gb300 import build as B
@@ -215,3 +216,16 @@ def test_phase_stability_of_the_other_cf_models(lib):
         assert e.value.status == S.SPFM_EINVAL
     finally:
         S.spfm_destroy_grid(h)
+
+
+def test_fp32_band_limits_are_the_floats_next_to_the_fp64_limits():
+    """The stats kernel tests an FP32 cell against the first float above 1e-6
+    and the last float below 1 - 1e-6 (hex literals in stats.cu); those are
+    the floats that select exactly the cells with 1e-6 < phi < 1 - 1e-6."""
+    src = open(os.path.join(ROOT, "paper_1910_05180_gb300", "csrc", "stats.cu")).read()
+    m = re.search(r"return x >= (0x[0-9a-fp.+-]+)f && x <= (0x[0-9a-fp.+-]+)f;", src)
+    lo, hi = float.fromhex(m.group(1)), float.fromhex(m.group(2))
+    f32 = np.float32
+    assert f32(lo) == lo and f32(hi) == hi
+    assert lo > 1e-6 and float(np.nextafter(f32(lo), f32(0))) <= 1e-6
+    assert hi < 1 - 1e-6 and float(np.nextafter(f32(hi), f32(1))) >= 1 - 1e-6
