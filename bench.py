@@ -269,8 +269,9 @@ def batched_vs_plain(n_grids: int, dev):
         cells = sum(j["nx"] * j["ny"] * j["nz"] for j in jobs)
         b = S.Batch(grids, stream=stream)
         b.step(16, args)
-        # work-list depth chosen by the autotuner (its trial steps are real steps)
+        # tile policy and work-list depth chosen by the autotuner (its trial steps are real steps)
         depth, depth_ms = b.autotune(args, steps_per_trial=32)
+        tiles = b.tiles()
         for g, a in zip(grids, args):
             g.step(2, lam=a.lam, dt=a.dt, dF=a.dF, stencil=26)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -306,6 +307,7 @@ def batched_vs_plain(n_grids: int, dev):
             "velocity_rel_err_p90": float(np.percentile(errs, 90)),
             "velocity_rel_err_max": float(errs.max()),
             "depth": depth, "depth_ms_per_step": {str(k): v for k, v in depth_ms.items()},
+            "tile_policy": {0: "wide 64x16", 1: "square 32x32", 2: "fit per grid"}[tiles[0]],
             "note": "batched and plain give bit-identical fields (tests/test_gpu_batch.py)"}
 
 

@@ -232,18 +232,35 @@ spfm_status spfm_batch_create(spfm_grid *const *grids, int n, void *scratch,
 /* n_steps steps of every grid with its own args[i]; all grids must share stencil and
  * scheme.  Replays a captured CUDA graph of the per-step launches. */
 spfm_status spfm_batch_step(spfm_batch *b, int n_steps, const spfm_step_args *args);
-/* Autotuner of the batch's work-list: the z-march depth of its items (planes
- * per item: 8, 12, 16, 24, 32, 48 or 64).  Each candidate is timed with CUDA
- * events over steps_per_trial steps (a multiple of 16, at least 16) after a
+/* Tile policies of a batch's work-list: the xy tile shape of each grid's items.
+ * FP32 batches have two shapes, 64 x 16 cells (the single-grid tile) and 32 x 32
+ * (for grids narrower than 64 cells or padded by the wide tile); FP64 and BF16
+ * batches have the first only and accept every policy.
+ *   SPFM_TILES_WIDE    every grid on 64 x 16 tiles
+ *   SPFM_TILES_SQUARE  every grid on 32 x 32 tiles
+ *   SPFM_TILES_FIT     each grid on the shape that pads its nx x ny extent least,
+ *                      ties to 64 x 16 (the default; the two shapes then run as
+ *                      two persistent launches per step) */
+enum { SPFM_TILES_WIDE = 0, SPFM_TILES_SQUARE = 1, SPFM_TILES_FIT = 2 };
+/* Autotuner of the batch's work-list: first the tile policy (FP32 batches: the
+ * three above, at the current depth), then the z-march depth of its items
+ * (planes per item: 8, 12, 16, 24, 32, 48 or 64).  Each candidate is timed with
+ * CUDA events over steps_per_trial steps (a multiple of 16, at least 16) after a
  * 16-step warm-up, all of them real steps of every grid with args, exactly as
- * spfm_batch_step would take them: the grids advance by 7 * (16 + steps_per_trial)
- * steps in all, and their fields do not depend on the depth chosen.  The
- * fastest depth is kept for later steps.  Needs a non-default stream (graphs).
- * out_depth (may be NULL) receives the depth chosen, out_ms (may be NULL, else
- * 7 doubles) the milliseconds per step of each candidate in the order above.
- * Synchronises the stream.  No counterpart in the paper. */
+ * spfm_batch_step would take them: the grids advance by (3 + 7) * (16 +
+ * steps_per_trial) steps in all for FP32 (7 * (...) otherwise), and their fields
+ * do not depend on the policy or depth chosen.  The fastest policy and depth are
+ * kept for later steps (spfm_batch_tiles reports them).  Needs a non-default
+ * stream (graphs).  out_depth (may be NULL) receives the depth chosen, out_ms
+ * (may be NULL, else 7 doubles) the milliseconds per step of each depth in the
+ * order above.  Synchronises the stream.  No counterpart in the paper. */
 spfm_status spfm_batch_autotune(spfm_batch *b, const spfm_step_args *args, int steps_per_trial,
                                 int *out_depth, double *out_ms);
+/* Set the tile policy of the batch's work-list (one of SPFM_TILES_*), keeping
+ * its depth; the fields do not depend on it.  Synchronises the stream. */
+spfm_status spfm_batch_set_tiles(spfm_batch *b, int policy);
+/* The batch's current tile policy and z-march depth (either may be NULL). */
+spfm_status spfm_batch_tiles(const spfm_batch *b, int *policy, int *depth);
 /* Diagnostics of every grid in one pass; out has n entries.  Synchronises. */
 spfm_status spfm_batch_stats(spfm_batch *b, int flags, spfm_stats *out);
 spfm_status spfm_batch_destroy(spfm_batch *b);

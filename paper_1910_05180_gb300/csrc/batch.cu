@@ -39,11 +39,25 @@ size_t grid_record_bytes(int dtype)
                              : (dtype == SPFM_F32 ? batch_grid_bytes_f32() : batch_grid_bytes_bf16());
 }
 
-int items_of(int dtype, const GridGeom &g, int gi, int depth, BatchItem *out)
+int items_of(int dtype, const GridGeom &g, int gi, int depth, BatchItem *out, int shape)
 {
-    return dtype == SPFM_F64   ? batch_items_f64(g, gi, depth, out)
-           : dtype == SPFM_F32 ? batch_items_f32(g, gi, depth, out)
-                               : batch_items_bf16(g, gi, depth, out);
+    return dtype == SPFM_F64   ? batch_items_f64(g, gi, depth, out, shape)
+           : dtype == SPFM_F32 ? batch_items_f32(g, gi, depth, out, shape)
+                               : batch_items_bf16(g, gi, depth, out, shape);
+}
+
+// Tile shapes of FP32 batch items: 0 = 64 x 16 cells (the single-grid tile),
+// 1 = 32 x 32.  A tile policy gives every grid one of them:
+//   SPFM_TILES_WIDE all 0, SPFM_TILES_SQUARE all 1, SPFM_TILES_FIT the shape
+//   whose tiles pad the grid's xy extent least (ties keep 0).
+// Other storage types have the one shape 0.
+int shape_for(int dtype, const GridGeom &g, int policy)
+{
+    if (dtype != SPFM_F32 || policy == SPFM_TILES_WIDE) return 0;
+    if (policy == SPFM_TILES_SQUARE) return 1;
+    const long long wide = (long long)((g.nx + 63) / 64 * 64) * ((g.ny + 15) / 16 * 16);
+    const long long sq = (long long)((g.nx + 31) / 32 * 32) * ((g.ny + 31) / 32 * 32);
+    return sq < wide ? 1 : 0;
 }
 
 Layout layout_for(int dtype, int n, int nitems)
@@ -78,10 +92,12 @@ int check_grids(spfm_grid *const *grids, int n, int *dtype, int *nitems)
             return fail(nullptr, SPFM_EINVAL, "spfm_batch: grid %d has another dtype", i);
         for (int j = 0; j < i; ++j)
             if (grids[j] == grids[i]) return fail(nullptr, SPFM_EINVAL, "spfm_batch: grid %d repeated", i);
-        items += items_of(grids[i]->d.dtype, grids[i]->geom, i, kMinDepth, nullptr);
+        const int a = items_of(grids[i]->d.dtype, grids[i]->geom, i, kMinDepth, nullptr, 0);
+        const int b = grids[i]->d.dtype == SPFM_F32 ? items_of(SPFM_F32, grids[i]->geom, i, kMinDepth, nullptr, 1) : 0;
+        items += a > b ? a : b;
     }
     *dtype = grids[0]->d.dtype;
-    *nitems = items;   // the longest work-list (shallowest depth): the scratch size
+    *nitems = items;   // the longest work-list (shallowest depth, either shape): the scratch size
     return SPFM_OK;
 }
 
@@ -89,7 +105,8 @@ int check_grids(spfm_grid *const *grids, int n, int *dtype, int *nitems)
 
 struct spfm_batch {
     std::vector<spfm_grid *> grids;
-    int n = 0, dtype = 0, nitems = 0, depth = kBatchZChunk;
+    int n = 0, dtype = 0, nitems = 0, depth = kBatchZChunk, policy = SPFM_TILES_FIT;
+    int nitems0 = 0;   // items of shape 0; the shape-1 items follow them in the list
     char *scratch = nullptr;
     cudaStream_t stream = nullptr;
     Layout L;
@@ -113,15 +130,26 @@ static int bfail(spfm_batch *b, int code, const char *msg)
     return fail(nullptr, code, "%s", msg);
 }
 
-// the work-list of z-march depth `depth`, uploaded on the batch's stream (the
-// captured graph holds the item count, so it is dropped)
+// the work-list of z-march depth `depth` under the batch's tile policy,
+// uploaded on the batch's stream (the captured graph holds the item count, so
+// it is dropped)
 static cudaError_t set_depth(spfm_batch *b, int depth)
 {
     int k = 0;
-    for (int i = 0; i < b->n; ++i) k += items_of(b->dtype, b->grids[i]->geom, i, depth, nullptr);
+    for (int i = 0; i < b->n; ++i) {
+        const GridGeom &g = b->grids[i]->geom;
+        k += items_of(b->dtype, g, i, depth, nullptr, shape_for(b->dtype, g, b->policy));
+    }
     b->h_items.resize(k);
     k = 0;
-    for (int i = 0; i < b->n; ++i) k += items_of(b->dtype, b->grids[i]->geom, i, depth, b->h_items.data() + k);
+    for (int shape = 0; shape < 2; ++shape) {   // shape 0 items first, one launch per shape
+        for (int i = 0; i < b->n; ++i) {
+            const GridGeom &g = b->grids[i]->geom;
+            if (shape_for(b->dtype, g, b->policy) == shape)
+                k += items_of(b->dtype, g, i, depth, b->h_items.data() + k, shape);
+        }
+        if (shape == 0) b->nitems0 = k;
+    }
     b->nitems = k;
     b->depth = depth;
     if (b->exec) {
@@ -132,17 +160,28 @@ static cudaError_t set_depth(spfm_batch *b, int depth)
                            cudaMemcpyHostToDevice, b->stream);
 }
 
-// one step of every grid: persistent step kernel, then the ghost faces of the
-// buffers it wrote
+// one step of every grid: persistent step kernel (one per tile shape in the
+// list), then the ghost faces of the buffers it wrote
 static cudaError_t launch_one(spfm_batch *b, int parity, int stencil, int kind)
 {
     const void *grids = b->scratch + b->L.grids;
     const BatchItem *items = (const BatchItem *)(b->scratch + b->L.items);
     int *err = (int *)(b->scratch + b->L.err);
     cudaError_t e;
-    if (b->dtype == SPFM_F64) e = launch_batch_f64(grids, items, b->nitems, parity, err, stencil, kind, b->stream);
-    else if (b->dtype == SPFM_F32) e = launch_batch_f32(grids, items, b->nitems, parity, err, stencil, kind, b->stream);
-    else e = launch_batch_bf16(grids, items, b->nitems, parity, err, stencil, kind, b->stream);
+    if (b->dtype == SPFM_F64) {
+        e = launch_batch_f64(grids, items, b->nitems, parity, err, stencil, kind, b->stream);
+    } else if (b->dtype == SPFM_F32) {
+        // the two tile shapes run as two persistent launches over their parts of
+        // the list (their grids differ, so the second needs nothing of the first)
+        e = cudaSuccess;
+        if (b->nitems0 > 0)
+            e = launch_batch_f32(grids, items, b->nitems0, parity, err, stencil, kind, b->stream, 0);
+        if (e == cudaSuccess && b->nitems > b->nitems0)
+            e = launch_batch_f32(grids, items + b->nitems0, b->nitems - b->nitems0, parity, err, stencil, kind,
+                                 b->stream, 1);
+    } else {
+        e = launch_batch_bf16(grids, items, b->nitems, parity, err, stencil, kind, b->stream);
+    }
     if (e != cudaSuccess) return e;
     return launch_fill_ghosts_batch((const GhostJob *)(b->scratch + b->L.ghosts), b->n, b->dtype,
                                     parity ^ 1, b->stream);
@@ -318,6 +357,35 @@ spfm_status spfm_batch_autotune(spfm_batch *b, const spfm_step_args *args, int s
         return bfail(b, SPFM_ECUDA, cudaGetErrorString(e));
     }
     spfm_status st = SPFM_OK;
+    // the tile policy first, at the current depth (FP32 only: one shape otherwise)
+    if (b->dtype == SPFM_F32) {
+        int best_policy = b->policy;
+        double best_pol_ms = 0.0;
+        const int policies[3] = {SPFM_TILES_WIDE, SPFM_TILES_SQUARE, SPFM_TILES_FIT};
+        for (int c = 0; c < 3 && st == SPFM_OK; ++c) {
+            b->policy = policies[c];
+            e = set_depth(b, b->depth);
+            if (e != cudaSuccess) {
+                st = bfail(b, SPFM_ECUDA, cudaGetErrorString(e));
+                break;
+            }
+            st = spfm_batch_step(b, kGraphSteps, args);
+            if (st != SPFM_OK) break;
+            e = cudaEventRecord(e0, b->stream);
+            if (e == cudaSuccess) st = spfm_batch_step(b, steps_per_trial, args);
+            if (e == cudaSuccess && st == SPFM_OK) e = cudaEventRecord(e1, b->stream);
+            if (e == cudaSuccess && st == SPFM_OK) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess && st == SPFM_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) st = bfail(b, SPFM_ECUDA, cudaGetErrorString(e));
+            if (st != SPFM_OK) break;
+            if (c == 0 || ms < best_pol_ms) {
+                best_pol_ms = ms;
+                best_policy = policies[c];
+            }
+        }
+        b->policy = best_policy;
+    }
     int best = kBatchZChunk;
     double best_ms = 0.0;
     for (int c = 0; c < kNDepths && st == SPFM_OK; ++c) {
@@ -350,6 +418,26 @@ spfm_status spfm_batch_autotune(spfm_batch *b, const spfm_step_args *args, int s
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bfail(b, SPFM_ECUDA, cudaGetErrorString(e));
     if (out_depth) *out_depth = best;
+    return SPFM_OK;
+}
+
+spfm_status spfm_batch_set_tiles(spfm_batch *b, int policy)
+{
+    if (!b) return fail(nullptr, SPFM_EINVAL, "spfm_batch_set_tiles: batch is NULL");
+    if (policy != SPFM_TILES_WIDE && policy != SPFM_TILES_SQUARE && policy != SPFM_TILES_FIT)
+        return bfail(b, SPFM_EINVAL, "spfm_batch_set_tiles: unknown tile policy");
+    b->policy = policy;
+    cudaError_t e = set_depth(b, b->depth);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, SPFM_ECUDA, cudaGetErrorString(e));
+    return SPFM_OK;
+}
+
+spfm_status spfm_batch_tiles(const spfm_batch *b, int *policy, int *depth)
+{
+    if (!b) return fail(nullptr, SPFM_EINVAL, "spfm_batch_tiles: batch is NULL");
+    if (policy) *policy = b->policy;
+    if (depth) *depth = b->depth;
     return SPFM_OK;
 }
 

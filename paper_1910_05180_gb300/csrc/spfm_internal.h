@@ -132,9 +132,9 @@ constexpr int kWaitFaces = 1, kWaitAll = 2, kImages = 4;
 
 // TMA tensor maps of a grid's two field buffers, encoded on first use (tma.cu).
 struct TmaCache {
-    CUtensorMap map[2];
-    const void *base[2];
-    int state[2];   // 0 not encoded, 1 encoded, -1 encoding unavailable (row copies)
+    CUtensorMap map[4];   // [buffer] for the single-grid box, [2 + buffer] for the square batch box
+    const void *base[4];
+    int state[4];   // 0 not encoded, 1 encoded, -1 encoding unavailable (row copies)
 };
 
 // Encode a 3D tiled map over a ghosted buffer with a (box_x, box_y, 1) box.
@@ -217,6 +217,7 @@ size_t grid_scratch_bytes();
 // One tile of a batch's packed work-list: grid, tile column/row, z range.
 struct BatchItem {
     int grid, bx, by, zc0, zc1;
+    int shape;   // tile shape of the item (0: the single-grid shape; 1: the square FP32 shape)
 };
 
 // Per-dtype pieces of the persistent batch kernel (step_f32.cu / ...):
@@ -226,14 +227,15 @@ struct BatchItem {
 size_t batch_grid_bytes_f32();
 size_t batch_grid_bytes_f64();
 size_t batch_grid_bytes_bf16();
-int batch_items_f32(const GridGeom &g, int grid_index, int zchunk, BatchItem *out);
-int batch_items_f64(const GridGeom &g, int grid_index, int zchunk, BatchItem *out);
-int batch_items_bf16(const GridGeom &g, int grid_index, int zchunk, BatchItem *out);
+// (shape 1 exists for FP32 only; the FP64 and BF16 items are always shape 0)
+int batch_items_f32(const GridGeom &g, int grid_index, int zchunk, BatchItem *out, int shape);
+int batch_items_f64(const GridGeom &g, int grid_index, int zchunk, BatchItem *out, int shape);
+int batch_items_bf16(const GridGeom &g, int grid_index, int zchunk, BatchItem *out, int shape);
 void batch_fill_grid_f32(void *slot, const StepCoef<float> &c, void *const field[2], int cur, TmaCache *tma);
 void batch_fill_grid_f64(void *slot, const StepCoef<double> &c, void *const field[2], int cur, TmaCache *tma);
 void batch_fill_grid_bf16(void *slot, const StepCoef<float> &c, void *const field[2], int cur, TmaCache *tma);
 cudaError_t launch_batch_f32(const void *grids, const BatchItem *work, int nwork, int parity, int *err,
-                             int stencil, int kind, cudaStream_t st);
+                             int stencil, int kind, cudaStream_t st, int shape);
 cudaError_t launch_batch_f64(const void *grids, const BatchItem *work, int nwork, int parity, int *err,
                              int stencil, int kind, cudaStream_t st);
 cudaError_t launch_batch_bf16(const void *grids, const BatchItem *work, int nwork, int parity, int *err,

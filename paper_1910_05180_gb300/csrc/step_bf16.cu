@@ -13,9 +13,9 @@ cudaError_t launch_step_bf16(const StepCoef<float> &c, const __nv_bfloat16 *src,
 
 size_t batch_grid_bytes_bf16() { return sizeof(BatchGrid<float>); }
 
-int batch_items_bf16(const GridGeom &g, int grid_index, int zchunk, BatchItem *out)
+int batch_items_bf16(const GridGeom &g, int grid_index, int zchunk, BatchItem *out, int)
 {
-    return batch_items_t<__nv_bfloat16, float, 8, 16>(g, grid_index, zchunk, out);
+    return batch_items_t<__nv_bfloat16, float, 8, 16>(g, grid_index, zchunk, out, 0);
 }
 
 void batch_fill_grid_bf16(void *slot, const StepCoef<float> &c, void *const field[2], int cur,
@@ -35,6 +35,7 @@ void batch_fill_grid_bf16(void *slot, const StepCoef<float> &c, void *const fiel
         b->map[0] = *m0;
         b->map[1] = *m1;
     }
+    b->has_map_sq = 0;
 }
 
 cudaError_t launch_batch_bf16(const void *grids, const BatchItem *work, int nwork, int parity,

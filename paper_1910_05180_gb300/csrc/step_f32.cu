@@ -8,6 +8,10 @@
 #ifndef SPFM_F32_TY
 #define SPFM_F32_TY 16
 #endif
+// the square tile of FP32 batch items of shape 1: 8 threads of 4 cells, 32 rows
+// (32 x 32 cells, the same 128 consumer threads), for grids narrower than the
+// 64-cell tile or whose x extent it would pad
+constexpr int kSqTX = 8, kSqTY = 32;
 
 namespace spfm {
 cudaError_t launch_step_f32(const StepCoef<float> &c, const float *src, float *dst, int *err,
@@ -21,9 +25,10 @@ cudaError_t launch_step_f32(const StepCoef<float> &c, const float *src, float *d
 
 size_t batch_grid_bytes_f32() { return sizeof(BatchGrid<float>); }
 
-int batch_items_f32(const GridGeom &g, int grid_index, int zchunk, BatchItem *out)
+int batch_items_f32(const GridGeom &g, int grid_index, int zchunk, BatchItem *out, int shape)
 {
-    return batch_items_t<float, float, SPFM_F32_TX, SPFM_F32_TY>(g, grid_index, zchunk, out);
+    if (shape == 1) return batch_items_t<float, float, kSqTX, kSqTY>(g, grid_index, zchunk, out, 1);
+    return batch_items_t<float, float, SPFM_F32_TX, SPFM_F32_TY>(g, grid_index, zchunk, out, 0);
 }
 
 void batch_fill_grid_f32(void *slot, const StepCoef<float> &c, void *const field[2], int cur,
@@ -43,11 +48,21 @@ void batch_fill_grid_f32(void *slot, const StepCoef<float> &c, void *const field
         b->map[0] = *m0;
         b->map[1] = *m1;
     }
+    using Sq = TileShape<float, float, kSqTX, kSqTY>;
+    const CUtensorMap *q0 = cached_map(tma, 2, c.g, SPFM_F32, field[0], Sq::SW, Sq::ROWS);
+    const CUtensorMap *q1 = cached_map(tma, 3, c.g, SPFM_F32, field[1], Sq::SW, Sq::ROWS);
+    b->has_map_sq = (q0 && q1) ? 1 : 0;
+    if (b->has_map_sq) {
+        b->map_sq[0] = *q0;
+        b->map_sq[1] = *q1;
+    }
 }
 
 cudaError_t launch_batch_f32(const void *grids, const BatchItem *work, int nwork, int parity,
-                              int *err, int stencil, int kind, cudaStream_t st)
+                              int *err, int stencil, int kind, cudaStream_t st, int shape)
 {
+    if (shape == 1)
+        return launch_batch_t<float, float, kSqTX, kSqTY, true>(grids, work, nwork, parity, err, stencil, kind, st);
     return launch_batch_t<float, float, SPFM_F32_TX, SPFM_F32_TY>(grids, work, nwork, parity, err, stencil, kind, st);
 }
 }  // namespace spfm

@@ -13,9 +13,9 @@ cudaError_t launch_step_f64(const StepCoef<double> &c, const double *src, double
 
 size_t batch_grid_bytes_f64() { return sizeof(BatchGrid<double>); }
 
-int batch_items_f64(const GridGeom &g, int grid_index, int zchunk, BatchItem *out)
+int batch_items_f64(const GridGeom &g, int grid_index, int zchunk, BatchItem *out, int)
 {
-    return batch_items_t<double, double, 16, 16>(g, grid_index, zchunk, out);
+    return batch_items_t<double, double, 16, 16>(g, grid_index, zchunk, out, 0);
 }
 
 void batch_fill_grid_f64(void *slot, const StepCoef<double> &c, void *const field[2], int cur,
@@ -35,6 +35,7 @@ void batch_fill_grid_f64(void *slot, const StepCoef<double> &c, void *const fiel
         b->map[0] = *m0;
         b->map[1] = *m1;
     }
+    b->has_map_sq = 0;
 }
 
 cudaError_t launch_batch_f64(const void *grids, const BatchItem *work, int nwork, int parity,

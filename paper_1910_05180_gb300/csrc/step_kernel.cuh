@@ -824,11 +824,14 @@ struct BatchGrid {
     void *field[2];
     int cur;                // buffer holding the field at parity 0
     int has_map;
+    CUtensorMap map_sq[2];  // the same for the box of the square tile shape (when has_map_sq)
+    int has_map_sq;
 };
 
-// Persistent kernel over the packed work-list of all grids of a batch: CTA b
-// takes items b, b + gridDim.x, ...  Step `parity` reads buffer cur ^ parity.
-template <class S, class T, int STENCIL, int KIND, int TX, int TY>
+// Persistent kernel over a packed work-list of items of one tile shape (TX,
+// TY): CTA b takes items b, b + gridDim.x, ...  Step `parity` reads buffer
+// cur ^ parity.  SQ: the items use the square tile's TMA maps (map_sq).
+template <class S, class T, int STENCIL, int KIND, int TX, int TY, bool SQ>
 __global__ void __launch_bounds__(TileShape<S, T, TX, TY>::NTHREADS, BatchMinBlocks<S>::value)
     spfm_batch_kernel(const BatchGrid<T> *__restrict__ grids, const BatchItem *__restrict__ work,
                       int nwork, int parity, int *__restrict__ err)
@@ -849,7 +852,7 @@ __global__ void __launch_bounds__(TileShape<S, T, TX, TY>::NTHREADS, BatchMinBlo
         const BatchItem it = work[w];
         const BatchGrid<T> &bg = grids[it.grid];
         const int cur = bg.cur ^ parity;
-        const CUtensorMap *map = bg.has_map ? &bg.map[cur] : nullptr;
+        const CUtensorMap *map = SQ ? (bg.has_map_sq ? &bg.map_sq[cur] : nullptr) : (bg.has_map ? &bg.map[cur] : nullptr);
         if (map && threadIdx.x == Sh::NCONS)
             asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
         const bool last = w + (int)gridDim.x >= nwork;
@@ -861,9 +864,10 @@ __global__ void __launch_bounds__(TileShape<S, T, TX, TY>::NTHREADS, BatchMinBlo
     }
 }
 
-// Work-list entries of one grid for the tile shape of the (S, T) kernel.
+// Work-list entries of one grid for the tile shape (TX, TY) of the (S, T)
+// kernel, marked with the item shape index `shape`.
 template <class S, class T, int TX, int TY>
-inline int batch_items_t(const GridGeom &g, int grid_index, int zchunk, BatchItem *out)
+inline int batch_items_t(const GridGeom &g, int grid_index, int zchunk, BatchItem *out, int shape = 0)
 {
     using Sh = TileShape<S, T, TX, TY>;
     const int gxn = (g.nx + Sh::W - 1) / Sh::W, gyn = (g.ny + TY - 1) / TY;
@@ -871,13 +875,13 @@ inline int batch_items_t(const GridGeom &g, int grid_index, int zchunk, BatchIte
     for (int z = 0; z < g.nz; z += zchunk)
         for (int by = 0; by < gyn; ++by)
             for (int bx = 0; bx < gxn; ++bx) {
-                if (out) out[n] = BatchItem{grid_index, bx, by, z, min(z + zchunk, g.nz)};
+                if (out) out[n] = BatchItem{grid_index, bx, by, z, min(z + zchunk, g.nz), shape};
                 ++n;
             }
     return n;
 }
 
-template <class S, class T, int TX, int TY>
+template <class S, class T, int TX, int TY, bool SQ = false>
 cudaError_t launch_batch_t(const void *grids, const BatchItem *work, int nwork, int parity, int *err,
                            int stencil, int kind, cudaStream_t st)
 {
@@ -890,7 +894,7 @@ cudaError_t launch_batch_t(const void *grids, const BatchItem *work, int nwork, 
     if (ctas < 1) return cudaSuccess;
     const BatchGrid<T> *bg = (const BatchGrid<T> *)grids;
 #define SPFM_BLAUNCH(ST, KD) \
-    spfm_batch_kernel<S, T, ST, KD, TX, TY><<<ctas, Sh::NTHREADS, 0, st>>>(bg, work, nwork, parity, err)
+    spfm_batch_kernel<S, T, ST, KD, TX, TY, SQ><<<ctas, Sh::NTHREADS, 0, st>>>(bg, work, nwork, parity, err)
 #define SPFM_BBY_KIND(ST)                      \
     do {                                       \
         if (kind == 0) SPFM_BLAUNCH(ST, 0);    \

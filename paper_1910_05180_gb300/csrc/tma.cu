@@ -51,7 +51,7 @@ int encode_field_map(CUtensorMap *map, const GridGeom &g, int dtype, const void 
 const CUtensorMap *cached_map(TmaCache *cache, int which, const GridGeom &g, int dtype,
                               const void *base, int box_x, int box_y)
 {
-    if (!cache || which < 0 || which > 1) return nullptr;
+    if (!cache || which < 0 || which > 3) return nullptr;
     if (cache->state[which] == 1 && cache->base[which] == base) return &cache->map[which];
     if (cache->state[which] == -1 && cache->base[which] == base) return nullptr;
     cache->base[which] = base;

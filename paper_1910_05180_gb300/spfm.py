@@ -28,6 +28,7 @@ SPFM_PERIODIC, SPFM_NOFLUX, SPFM_CONTACT = 0, 1, 2
 SPFM_TI_GLOBAL, SPFM_TI_LOCAL, SPFM_FD = 0, 1, 2
 SPFM_FD_H5, SPFM_FD_HABEL = 3, 4   # CF with the interpolation functions h5 and h_Abel (Tab. 2)
 SPFM_STATS_ENERGY = 1
+SPFM_TILES_WIDE, SPFM_TILES_SQUARE, SPFM_TILES_FIT = 0, 1, 2   # batch tile policies
 
 TORCH_DTYPE = {SPFM_F64: torch.float64, SPFM_F32: torch.float32, SPFM_BF16: torch.bfloat16}
 STATUS_NAME = {0: "SPFM_OK", -1: "SPFM_EINVAL", -2: "SPFM_EUNSTABLE", -3: "SPFM_EPHASE",
@@ -106,6 +107,8 @@ SIGNATURES = [
     ("spfm_batch_step", _I, [_P, _I, ctypes.POINTER(StepArgs)]),
     ("spfm_batch_autotune", _I, [_P, ctypes.POINTER(StepArgs), _I, ctypes.POINTER(ctypes.c_int),
                                  ctypes.POINTER(ctypes.c_double)]),
+    ("spfm_batch_set_tiles", _I, [_P, _I]),
+    ("spfm_batch_tiles", _I, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     ("spfm_batch_stats", _I, [_P, _I, ctypes.POINTER(Stats)]),
     ("spfm_batch_destroy", _I, [_P]),
 ]
@@ -370,6 +373,16 @@ def spfm_batch_step(b, n_steps, args):
 BATCH_DEPTHS = (8, 12, 16, 24, 32, 48, 64)   # z-march depths the autotuner tries
 
 
+def spfm_batch_set_tiles(b, policy):
+    _check(load().spfm_batch_set_tiles(b, int(policy)))
+
+
+def spfm_batch_tiles(b):
+    policy, depth = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().spfm_batch_tiles(b, ctypes.byref(policy), ctypes.byref(depth)))
+    return policy.value, depth.value
+
+
 def spfm_batch_autotune(b, args, steps_per_trial=32):
     arr = (StepArgs * len(args))(*args)
     depth = ctypes.c_int(0)
@@ -415,10 +428,19 @@ class Batch:
         spfm_batch_step(self.handle, n_steps, args)
 
     def autotune(self, args, steps_per_trial=32):
-        """Pick the work-list depth by timing each candidate on real steps (the
-        grids advance by len(BATCH_DEPTHS) * (16 + steps_per_trial) steps).
-        Returns (depth, {depth: ms per step})."""
+        """Pick the tile policy (FP32) and then the work-list depth by timing each
+        candidate on real steps (the grids advance by (3 + len(BATCH_DEPTHS)) *
+        (16 + steps_per_trial) steps for FP32).  Returns (depth, {depth: ms per
+        step}); tiles() gives the policy kept."""
         return spfm_batch_autotune(self.handle, args, steps_per_trial)
+
+    def set_tiles(self, policy):
+        """SPFM_TILES_WIDE, SPFM_TILES_SQUARE or SPFM_TILES_FIT (the fields do not depend on it)."""
+        spfm_batch_set_tiles(self.handle, policy)
+
+    def tiles(self):
+        """(tile policy, z-march depth) of the work-list."""
+        return spfm_batch_tiles(self.handle)
 
     def stats(self, flags=0, allow_nonfinite=False):
         return spfm_batch_stats(self.handle, len(self.grids), flags, allow_nonfinite)

@@ -110,9 +110,33 @@ def test_batch_rejects_mixed_stencils():
         assert e.value.status == S.SPFM_EINVAL
 
 
+@pytest.mark.parametrize("policy", [S.SPFM_TILES_WIDE, S.SPFM_TILES_SQUARE, S.SPFM_TILES_FIT])
+def test_tile_policies_equal_single_grids_bitwise(policy):
+    """The tile shape of a grid's items (64 x 16 or 32 x 32 cells, or per grid
+    the one that pads its extent least, here a mix) changes only the
+    work-list: after graph replays and an odd remainder the fields are
+    bit-identical to the same grids stepped alone."""
+    jobs = _jobs(7)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        batched = _grids(jobs, S.SPFM_F32, stream)
+        alone = _grids(jobs, S.SPFM_F32, stream)
+        b = S.Batch(batched, stream=stream)
+        b.set_tiles(policy)
+        assert b.tiles()[0] == policy
+        args = _args(jobs)
+        b.step(37, args)
+        for g, a in zip(alone, args):
+            g.step(37, lam=a.lam, dt=a.dt, dF=a.dF, stencil=26)
+        stream.synchronize()
+        for gb, ga in zip(batched, alone):
+            assert torch.equal(gb.get_field(), ga.get_field())
+
+
 def test_autotuned_batch_equals_single_grids_bitwise():
-    """The autotuner's trial steps are real steps, and the depth it picks
-    changes only the work-list: fields stay bit-identical to single grids."""
+    """The autotuner's trial steps are real steps, and the tile policy and
+    depth it picks change only the work-list: fields stay bit-identical to
+    single grids."""
     jobs = _jobs(5)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -122,7 +146,8 @@ def test_autotuned_batch_equals_single_grids_bitwise():
         args = _args(jobs)
         depth, ms = b.autotune(args, steps_per_trial=16)
         assert depth in S.BATCH_DEPTHS and all(v > 0.0 for v in ms.values())
-        tuned = len(S.BATCH_DEPTHS) * 32
+        assert b.tiles() in [(p, depth) for p in (S.SPFM_TILES_WIDE, S.SPFM_TILES_SQUARE, S.SPFM_TILES_FIT)]
+        tuned = (3 + len(S.BATCH_DEPTHS)) * 32
         b.step(21, args)
         for g, a in zip(alone, args):
             g.step(tuned + 21, lam=a.lam, dt=a.dt, dF=a.dF, stencil=26)
