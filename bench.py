@@ -76,6 +76,20 @@ def workload(args):
     return w
 
 
+SCHEME_NAME = {"ti120": "TI_<120>", "fd": "CF+h3", "local": "TI_n"}
+
+
+def arm_config(args, w, ws):
+    """The `config` of the JSON line, the same for the GPU arm and the oracle arm."""
+    cells = w["nx"] * w["ny"] * w["nz"]
+    return {"workload": w["name"] + f"_{args.scheme}_{args.dtype}_27pt",
+            "grid": [w["nx"], w["ny"], w["nz"]], "stencil": 27, "scheme": SCHEME_NAME[args.scheme],
+            "lambda": w["lam"], "dt": w["dt"], "dF": w["dF"], "bc": "periodic",
+            "stats_every": STATS_EVERY,
+            "l2": "inputs larger than L2 (two %d MB fields)" % (cells * BYTES_PER_UPDATE[args.dtype] // 2 // 2**20),
+            "parallelism": "replicas" if ws > 1 else "single"}
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -170,11 +184,12 @@ def profiled_traffic(kernel_key: str):
 # ------------------------------------------------------------------ oracle arm
 
 
-def _oracle_slab(w, nz_slab):
+def _oracle_slab(w, nz_slab, scheme="ti120"):
     import oracle as O
+    osch = {"ti120": O.TI_GLOBAL, "fd": O.CF, "local": O.TI_LOCAL}[scheme]
     p = O.Params(w["nx"], w["ny"], nz_slab, bc=(O.PERIODIC,) * 4 + (O.NOFLUX, O.NOFLUX),
                  n=w["u"], lam=w["lam"], dx=w["dx"], M=w["M"], Gamma=w["Gamma"], dt=w["dt"],
-                 dF=w["dF"], stencil=w["stencil"], scheme=O.TI_GLOBAL)
+                 dF=w["dF"], stencil=w["stencil"], scheme=osch)
     # the slab is the z-range around the grain's centre plane
     phi = O.init_sphere(p, (w["ctr"][0], w["ctr"][1], (nz_slab - 1) / 2.0), w["R"])
     return p, phi
@@ -217,7 +232,7 @@ def run_reference(args):
     # each timed step is one oracle step on a slab sized so that warm-up plus
     # timed steps take about 90 s of host time
     nz_slab = oracle_slab_for(w, 90.0 / max(1, args.steps + args.warmup))
-    p, phi = _oracle_slab(w, nz_slab)
+    p, phi = _oracle_slab(w, nz_slab, args.scheme)
     for _ in range(args.warmup):
         phi = O.step(p, phi, 1)
     per_step = []
@@ -234,9 +249,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": w["name"] + "_ti120_27pt", "grid": [w["nx"], w["ny"], w["nz"]],
-                       "sample_grid": [w["nx"], w["ny"], nz_slab], "stencil": 27,
-                       "scheme": "TI_<120>", "l2": "n/a (host)"},
+            "config": arm_config(args, w, ws),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -750,13 +763,7 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-            "config": {"workload": w["name"] + f"_{args.scheme}_{args.dtype}_27pt",
-                       "grid": [w["nx"], w["ny"], w["nz"]], "stencil": 27,
-                       "scheme": {"ti120": "TI_<120>", "fd": "CF+h3", "local": "TI_n"}[args.scheme],
-                       "lambda": w["lam"], "dt": w["dt"], "dF": w["dF"], "bc": "periodic",
-                       "stats_every": STATS_EVERY,
-                       "l2": "inputs larger than L2 (two %d MB fields)" % (cells * bpu // 2 // 2**20),
-                       "parallelism": "replicas" if ws > 1 else "single"},
+            "config": arm_config(args, w, ws),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": profiled_traffic(kernel_key),
