@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-friction", action="store_true", help="skip the 1D friction study")
     ap.add_argument("--no-force-scan", action="store_true", help="skip the force-oscillation scan")
     ap.add_argument("--no-kinetic", action="store_true", help="skip the 3D kinetic-anisotropy study")
+    ap.add_argument("--no-tilted", action="store_true", help="skip the 256^3 tilted-plane FP32/FP64 leg")
     ap.add_argument("--n", type=int, default=512, help="grid edge")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -591,6 +592,49 @@ def bf16_variant(w, dev, steps: int = 100):
     return out
 
 
+def tilted_256(dev, steps: int = 50, window: int = 400):
+    """The 256^3 tilted-plane configuration (normal (1,1,1)/sqrt3 through the
+    centre, contact faces, 27-point, lambda = 3 of its {2, 3, 4}) in FP32 and
+    FP64 storage, TI_<111> and CF + h3: step rate over `steps` steps, fraction of
+    the HBM roofline (8 or 16 B per update), and the velocity error against
+    v_th = -M dF/Gamma between steps 200 and 200 + window (the first-order time
+    discretisation error included: the GPU-vs-oracle velocity bar is a test)."""
+    import torch
+    from paper_1910_05180_gb300 import spfm as S
+    from paper_1910_05180_gb300 import workloads as WL
+    w = WL.tilted_111_256cubed()[1]
+    peak, _ = measured_hbm_peak()
+    cells = w["nx"] * w["ny"] * w["nz"]
+    stream = torch.cuda.Stream(device=dev)
+    out = {}
+    with torch.cuda.stream(stream):
+        for dname, dt_, bpu in (("f32", S.SPFM_F32, 8), ("f64", S.SPFM_F64, 16)):
+            for sname, sch in (("TI_<111>", S.SPFM_TI_GLOBAL), ("CF+h3", S.SPFM_FD)):
+                g = S.Grid(w["nx"], w["ny"], w["nz"], dtype=dt_, bc=(S.SPFM_CONTACT,) * 6, n=w["n"],
+                           stream=stream)
+                g.init_planar(w["c"], w["lam"], w["dx"])
+                kw = dict(lam=w["lam"], dx=w["dx"], dt=w["dt"], dF=w["dF"], stencil=26, scheme=sch)
+                g.step(5, **kw)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize(dev)
+                e0.record(stream)
+                g.step(steps, **kw)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ms = e0.elapsed_time(e1) / steps
+                g.step(200 - 5 - steps, **kw)
+                p1 = g.stats()["position"]
+                g.step(window, **kw)
+                p2 = g.stats()["position"]
+                v = (p2 - p1) / (window * w["dt"])
+                out[f"{sname}_{dname}"] = {"cell_updates_per_s": cells / (ms / 1e3), "ms_per_step": ms,
+                                           "frac_hbm": cells * bpu / (ms / 1e3) / 1e9 / peak,
+                                           "velocity_rel_err_vs_v_th": abs(v / (-w["dF"]) - 1.0)}
+                g.close()
+    out["workload"] = w["name"] + "_contact_27pt"
+    return out
+
+
 def serving_run(n_jobs: int):
     """Poisson stream (200 jobs/s) of velocity-measurement jobs, edges 32..192,
     continuous batching under a 120 GB budget, retirement at |dv/v| < 1e-4."""
@@ -707,6 +751,9 @@ def run_gpu(args):
     bf16 = None
     if rank == 0 and not args.no_bf16 and args.dtype != "bf16":
         bf16 = bf16_variant(w, dev)
+    tilted = None
+    if rank == 0 and not args.no_tilted:
+        tilted = tilted_256(dev)
     relax = None
     if rank == 0 and not args.no_relax:
         relax = shape_relaxation(dev)
@@ -773,7 +820,7 @@ def run_gpu(args):
                                    if per_step == 1 else "per step: stencil kernel + ghost-face kernel")
                                   + " (events around 50-step chunks)"},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
-            "batched": batched, "serving": serving, "grain_sphericity": grain, "variants": variants, "bf16_storage": bf16, "shape_relaxation": relax, "friction_1d": friction, "force_oscillation": force_scan, "kinetic_anisotropy": kinetic,
+            "batched": batched, "serving": serving, "grain_sphericity": grain, "variants": variants, "bf16_storage": bf16, "tilted_256": tilted, "shape_relaxation": relax, "friction_1d": friction, "force_oscillation": force_scan, "kinetic_anisotropy": kinetic,
             "last_stats": stats_seen[-1] if stats_seen else None,
             "stats_call": {"ms": (total_ms - step_ms) / max(1, len(stats_seen)), "every": STATS_EVERY,
                            "note": "interface stats between step chunks, host round trip included"},
