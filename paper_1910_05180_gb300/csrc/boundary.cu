@@ -62,9 +62,9 @@ __device__ __forceinline__ void ghost_faces(const FaceArgs &a, S *f, long long t
         const int sy = map_axis(j, g.ny, g.bc[2], g.bc[3], &fy, 2);
         const int sz = map_axis(k, g.nz, g.bc[4], g.bc[5], &fz, 4);
         T v = ld_ct(f, cell_index(g, sx, sy, sz));
-        if (fx >= 0) v = contact_shift<T>(v, (T)a.aface[fx]);
-        if (fy >= 0) v = contact_shift<T>(v, (T)a.aface[fy]);
-        if (fz >= 0) v = contact_shift<T>(v, (T)a.aface[fz]);
+        if (fx >= 0) v = contact_shift_rn(v, (T)a.aface[fx]);
+        if (fy >= 0) v = contact_shift_rn(v, (T)a.aface[fy]);
+        if (fz >= 0) v = contact_shift_rn(v, (T)a.aface[fz]);
         st_ct(f, cell_index(g, i, j, k), v);
     }
 }

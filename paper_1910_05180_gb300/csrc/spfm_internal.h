@@ -113,6 +113,21 @@ __host__ __device__ inline T contact_shift(T v, T a)
 {
     return (T(1) - a) * v / (T(1) - a * (T(2) * v - T(1)));
 }
+// The same with every operation rounded on its own (no contraction into FMAs),
+// so that the ghost layer is a fixed function of the interior, bit for bit
+// (the face kernel uses it).
+#ifdef __CUDACC__
+__device__ inline float contact_shift_rn(float v, float a)
+{
+    const float d = __fsub_rn(1.0f, __fmul_rn(a, __fsub_rn(__fmul_rn(2.0f, v), 1.0f)));
+    return __fdiv_rn(__fmul_rn(__fsub_rn(1.0f, a), v), d);
+}
+__device__ inline double contact_shift_rn(double v, double a)
+{
+    const double d = __dsub_rn(1.0, __dmul_rn(a, __dsub_rn(__dmul_rn(2.0, v), 1.0)));
+    return __ddiv_rn(__dmul_rn(__dsub_rn(1.0, a), v), d);
+}
+#endif
 
 
 // ---------------------------------------------------------------- launchers

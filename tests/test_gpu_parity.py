@@ -5,6 +5,8 @@ within 1e-4 relative.  Sizes span several tiles with ragged tails; the
 full-size cases compare sampled cells against oracle runs on their dependency
 cones.
 """
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -152,6 +154,74 @@ def test_periodic_ghost_layer_is_the_exact_wrap(dtype, shape):
         g.step(steps, lam=2.5, dt=0.05, dF=0.03, stencil=26)
         full = g.current_with_ghosts().double().cpu().numpy()
         assert np.array_equal(full, np.pad(full[1:-1, 1:-1, 1:-1], 1, mode="wrap"))
+
+
+def _ghosted_reference(phi, bc, n, lam, dx, dtype):
+    """The ghost layer the face rule gives, built in numpy in the storage
+    precision: periodic wrap, no-flux copy of the face cell, contact shift
+    (1 - a) v / (1 - a (2 v - 1)) with a = tanh(2 s dx n_axis / lambda) (s = -1
+    on the low face), every operation rounded on its own, axes x, y, z in turn."""
+    ft = np.float32 if dtype == S.SPFM_F32 else np.float64
+    nz, ny, nx = phi.shape
+    sizes = (nx, ny, nz)
+    idx, hit = [], []
+    for ax, N in enumerate(sizes):
+        c = np.arange(-1, N + 1)
+        src = np.clip(c, 0, N - 1)
+        face = np.full(c.shape, -1)
+        if bc[2 * ax] == S.SPFM_PERIODIC:
+            src = c % N
+        else:
+            if bc[2 * ax] == S.SPFM_CONTACT:
+                face[0] = 2 * ax
+            if bc[2 * ax + 1] == S.SPFM_CONTACT:
+                face[-1] = 2 * ax + 1
+        idx.append(src)
+        hit.append(face)
+    v = phi.astype(ft)[np.ix_(idx[2], idx[1], idx[0])]
+    # the host library's libm tanh, as the C library computes the couplings
+    a = [ft(math.tanh(2.0 * (-1.0 if f % 2 == 0 else 1.0) * dx * float(n[f // 2]) / lam)) for f in range(6)]
+    one, two = ft(1), ft(2)
+    for ax in range(3):
+        shape = [1, 1, 1]
+        shape[2 - ax] = sizes[ax] + 2
+        fh = hit[ax].reshape(shape)
+        for f in (2 * ax, 2 * ax + 1):
+            m = np.broadcast_to(fh == f, v.shape)
+            if not m.any():
+                continue
+            x = v[m]
+            d = one - a[f] * (two * x - one)
+            v[m] = ((one - a[f]) * x) / d
+    return v
+
+
+@pytest.mark.parametrize("dtype", [S.SPFM_F64, S.SPFM_F32])
+@pytest.mark.parametrize("shape,bc", [
+    ((48, 5, 3), (S.SPFM_CONTACT,) * 6),
+    ((64, 2, 1), (S.SPFM_NOFLUX, S.SPFM_CONTACT, S.SPFM_PERIODIC, S.SPFM_PERIODIC, S.SPFM_CONTACT, S.SPFM_NOFLUX)),
+    ((136, 33, 4), (S.SPFM_PERIODIC, S.SPFM_PERIODIC, S.SPFM_CONTACT, S.SPFM_CONTACT, S.SPFM_NOFLUX, S.SPFM_NOFLUX)),
+    ((20, 6, 5), (S.SPFM_CONTACT,) * 6),
+    ((48, 7, 3), (S.SPFM_PERIODIC,) * 6),    # the step kernel's images
+])
+def test_ghost_layer_matches_the_face_rule_exactly(dtype, shape, bc):
+    """After every step the whole ghost layer (faces, edges, corners) holds the
+    face rule applied to the interior, bit for bit: periodic, no-flux and
+    contact faces in every combination (the face kernel), and all-periodic
+    rows of whole 32-byte sectors (the step kernel's images)."""
+    nx, ny, nz = shape
+    n = rng_normal(43)
+    lam = 2.5
+    g, p = make_pair(nx, ny, nz, dtype, bc, n, lam=lam)
+    rng = np.random.default_rng(44)
+    phi0 = O.init_planar(p, float(n @ (np.array(shape) - 1) / 2.0)) + 0.01 * rng.random(p.shape)
+    upload(g, phi0, dtype)
+    for steps in (1, 2, 5):
+        g.step(steps, lam=lam, dt=0.05, dF=0.03, stencil=26)
+        full = g.current_with_ghosts().double().cpu().numpy()
+        want = _ghosted_reference(full[1:-1, 1:-1, 1:-1], bc, n, lam, 1.0, dtype).astype(np.float64)
+        bad = np.argwhere(full != want)
+        assert bad.size == 0, (len(bad), bad[:4].tolist(), np.abs(full - want).max())
 
 
 def test_periodic_image_steps_around_conserving_steps():
