@@ -38,7 +38,7 @@ STATS_EVERY = 50
 BYTES_PER_UPDATE = {"f32": 8, "f64": 16, "bf16": 4}   # one read + one write of phi per step
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3000)
@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--batch-only", action="store_true",
                     help="only the batched sweep: build it, 32 + 64 steps, print its rate (a small "
                          "command to profile the batch kernel)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def workload(args):
@@ -96,6 +96,24 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(ms: float, ws: int, device) -> float:
+    """The largest of the ranks' times (all-reduce MAX over the default process
+    group when ws > 1): the job's time is its slowest replica's."""
+    if ws <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(cells: int, steps: int, ws: int, max_ms: float) -> float:
+    """Whole-job cell-updates/s of ws independent replicas: every rank's cells
+    and steps over the slowest rank's time."""
+    return ws * cells * steps / (max_ms / 1e3)
 
 
 class ClockSampler:
@@ -710,14 +728,9 @@ def run_gpu(args):
     t_end.record(stream)
     barrier()
     clk = clocks.stop()
-    total_ms = t_start.elapsed_time(t_end)
+    total_ms = max_over_ranks(t_start.elapsed_time(t_end), ws, dev)
     step_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * cells * args.steps / (total_ms / 1e3)
+    value = replica_value(cells, args.steps, ws, total_ms)
     avg_kernel_ms = step_ms / args.steps
     bpu = BYTES_PER_UPDATE[args.dtype]
     peak, peak_kind = measured_hbm_peak()
@@ -786,9 +799,9 @@ def run_gpu(args):
             S.spfm_get_field(g.handle, host_out.data_ptr(), 1)
         t1.record(stream)
         barrier()
-        e_ms = t0.elapsed_time(t1)
+        e_ms = max_over_ranks(t0.elapsed_time(t1), ws, dev)
         fb = host_in.numel() * host_in.element_size()
-        e2e = {"value": ws * cells * E2E_STEPS * iters / (e_ms / 1e3), "unit": UNIT,
+        e2e = {"value": replica_value(cells, E2E_STEPS * iters, ws, e_ms), "unit": UNIT,
                "h2d_bytes_per_step": fb / E2E_STEPS, "d2h_bytes_per_step": (fb + 96) / E2E_STEPS,
                "note": f"per call: host field in, {E2E_STEPS} steps, stats, host field out"}
 
