@@ -58,7 +58,7 @@ def parse(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain sweep")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
-    ap.add_argument("--serve-jobs", type=int, default=300)
+    ap.add_argument("--serve-jobs", type=int, default=2000)
     ap.add_argument("--sweep-grids", type=int, default=256)
     ap.add_argument("--batch-only", action="store_true",
                     help="only the batched sweep: build it, 32 + 64 steps, print its rate (a small "
