@@ -68,3 +68,13 @@ def test_oracle_arm_runs_on_rank_0_only(monkeypatch):
     with redirect_stdout(buf):
         assert bench.run_reference(args) == 0
     assert buf.getvalue() == ""
+
+
+def test_both_arms_report_the_same_config():
+    """The oracle arm times the same workload as the GPU arm: one config dict."""
+    args = bench.parse([])
+    w = bench.workload(args)
+    cfg = bench.arm_config(args, w, 1)
+    assert cfg["workload"] == "sphere_512cubed_R150_ti120_f32_27pt"
+    assert cfg["grid"] == [512, 512, 512] and cfg["scheme"] == "TI_<120>" and cfg["bc"] == "periodic"
+    assert bench.arm_config(bench.parse(["--impl", "reference"]), w, 1) == cfg
