@@ -36,6 +36,7 @@ METRIC = ("SPFM cell-updates/s and % HBM roofline (1 GB300); batched/served vs p
 UNIT = "cell-updates/s"
 STATS_EVERY = 50
 BYTES_PER_UPDATE = {"f32": 8, "f64": 16, "bf16": 4}   # one read + one write of phi per step
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e nominal bandwidth, for context beside the measured peak
 
 
 def parse(argv=None):
@@ -826,6 +827,7 @@ def run_gpu(args):
             "config": arm_config(args, w, ws),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
+                         "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                          "traffic": profiled_traffic(kernel_key),
                          "kernel": "spfm_step_kernel", "bytes_per_update": bpu,
                          "avg_launch_ms": avg_kernel_ms,
