@@ -144,7 +144,9 @@ spfm_status spfm_init_cube(spfm_grid *g, const double ctr[3], double half, doubl
  * local normal, or CF).  stencil in {6, 18, 26}.  Validates first:
  * SPFM_EINVAL, SPFM_EUNSTABLE (dt above 2 / bound of the Jacobian's spectral
  * radius), SPFM_EPHASE (CF and |dF dx/Gamma| >= 8/(3 C_Gamma lambda/dx),
- * Sec. 3.1).  Asynchronous on the grid's stream. */
+ * Sec. 3.1).  Asynchronous on the grid's stream: one kernel launch per step
+ * when the step kernel writes the ghost layer itself, else two (see
+ * spfm_kernels_per_step). */
 spfm_status spfm_step(spfm_grid *g, int n_steps, double M, double Gamma, double lambda,
                       double dx, double dt, double dF, int stencil, int scheme);
 
