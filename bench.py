@@ -186,9 +186,9 @@ def source_hash(names=STEP_SOURCES):
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel_key: str):
-    """DRAM bytes per launch from the committed ncu summary, only while the
-    kernel sources are unchanged since the capture."""
+def profiled_record(kernel_key: str, field: str):
+    """A figure of the committed ncu summaries (profiles/traffic.json), only
+    while the kernel sources are unchanged since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -198,7 +198,12 @@ def profiled_traffic(kernel_key: str):
     e = d.get(kernel_key)
     if not e or e.get("source_hash") != source_hash():
         return None
-    return e.get("bytes_per_launch")
+    return e.get(field)
+
+
+def profiled_traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary."""
+    return profiled_record(kernel_key, "bytes_per_launch")
 
 
 # ------------------------------------------------------------------ oracle arm
@@ -761,6 +766,13 @@ def run_gpu(args):
             ms = e0.elapsed_time(e1) / nvar
             variants[name] = {"cell_updates_per_s": cells / (ms / 1e3), "ms_per_step": ms,
                               "frac_hbm": cells * bpu / (ms / 1e3) / 1e9 / peak}
+            if sch == S.SPFM_TI_LOCAL:
+                # TI_n is bound by the FP32 pipe: its ceiling from the committed
+                # capture (rate under ncu / FMA-pipe occupancy there)
+                ceil = profiled_record(f"spfm_step_kernel_{args.dtype}_27pt_local", "alu_ceiling_cell_updates_per_s")
+                variants[name]["bound"] = "alu"
+                variants[name]["alu_ceiling_cell_updates_per_s"] = ceil
+                variants[name]["frac_alu"] = cells / (ms / 1e3) / ceil if ceil else None
 
     bf16 = None
     if rank == 0 and not args.no_bf16 and args.dtype != "bf16":
