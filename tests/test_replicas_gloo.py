@@ -1,4 +1,5 @@
-"""The multi-rank host logic of the benchmark on CPU: two gloo ranks.
+"""Host logic of the benchmark on the CPU: two gloo ranks, the shared config,
+the profiled records.
 
 Every box here has one GPU, so N > 1 runs independent replicas, one per rank:
 the job's time is the slowest rank's (all-reduce MAX) and its throughput is all
@@ -78,3 +79,13 @@ def test_both_arms_report_the_same_config():
     assert cfg["workload"] == "sphere_512cubed_R150_ti120_f32_27pt"
     assert cfg["grid"] == [512, 512, 512] and cfg["scheme"] == "TI_<120>" and cfg["bc"] == "periodic"
     assert bench.arm_config(bench.parse(["--impl", "reference"]), w, 1) == cfg
+
+
+def test_profiled_figures_only_for_the_captured_sources(monkeypatch):
+    """The traffic and ALU-ceiling records of profiles/traffic.json are used
+    only while the stencil sources hash to the captured version."""
+    key = "spfm_step_kernel_f32_27pt_ti120_512"
+    assert bench.profiled_traffic(key) is not None
+    assert bench.profiled_record("spfm_step_kernel_f32_27pt_local", "alu_ceiling_cell_updates_per_s") > 0
+    monkeypatch.setattr(bench, "source_hash", lambda names=None: "0000000000000000")
+    assert bench.profiled_traffic(key) is None
