@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -37,6 +38,45 @@ UNIT = "cell-updates/s"
 STATS_EVERY = 50
 BYTES_PER_UPDATE = {"f32": 8, "f64": 16, "bf16": 4}   # one read + one write of phi per step
 NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e nominal bandwidth, for context beside the measured peak
+
+
+def finite_json(obj):
+    """obj with every non-finite float (NaN, +-Inf) replaced by None and numpy
+    scalars made plain, so that the line is strict JSON."""
+    if isinstance(obj, np.generic):
+        obj = obj.item()
+    if isinstance(obj, float):
+        return obj if math.isfinite(obj) else None
+    if isinstance(obj, dict):
+        return {str(k): finite_json(v) for k, v in obj.items()}
+    if isinstance(obj, (list, tuple)):
+        return [finite_json(v) for v in obj]
+    return obj
+
+
+def dumps(line) -> str:
+    return json.dumps(finite_json(line), allow_nan=False)
+
+
+def emit(line):
+    print(dumps(line), flush=True)
+
+
+# the keys of the final (headline) line; every study leg goes out before it as
+# a line of its own ({"leg": name, ...}), so the headline stays short
+HEADLINE_KEYS = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                 "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "roofline",
+                 "cpu_baseline", "e2e", "clocks", "gpu_launches", "stats_call", "legs")
+
+
+def headline(line: dict) -> dict:
+    return {k: line[k] for k in HEADLINE_KEYS if k in line}
+
+
+def stats_cadence(steps: int) -> int:
+    """Steps between two stats calls of the timed region: every STATS_EVERY
+    steps, and at least once in any run."""
+    return max(1, min(STATS_EVERY, steps))
 
 
 def parse(argv=None):
@@ -87,7 +127,7 @@ def arm_config(args, w, ws):
     return {"workload": w["name"] + f"_{args.scheme}_{args.dtype}_27pt",
             "grid": [w["nx"], w["ny"], w["nz"]], "stencil": 27, "scheme": SCHEME_NAME[args.scheme],
             "lambda": w["lam"], "dt": w["dt"], "dF": w["dF"], "bc": "periodic",
-            "stats_every": STATS_EVERY,
+            "stats_every": stats_cadence(args.steps),
             "l2": "inputs larger than L2 (two %d MB fields)" % (cells * BYTES_PER_UPDATE[args.dtype] // 2 // 2**20),
             "parallelism": "replicas" if ws > 1 else "single"}
 
@@ -118,24 +158,75 @@ def replica_value(cells: int, steps: int, ws: int, max_ms: float) -> float:
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms.  The sampler
+    starts before the warm-up; `mark(t0, t1)` gives the host wall-clock bounds
+    of the timed region, and the summary keeps the samples that fall inside it
+    (widened by one sampling period on each side, since a short timed region
+    may see none otherwise)."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 100
 
     def __init__(self, gpu_index: int):
         self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.proc = None
         self.gpu = gpu_index
+        self.window = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+                 "-lms", str(self.PERIOD_MS)], stdout=self.file, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+
+    def wait_live(self, timeout_s: float = 5.0):
+        """Return once the sampler has written its first sample (or after timeout_s)."""
+        if self.proc is None:
+            return
+        t_end = time.time() + timeout_s
+        while time.time() < t_end and os.path.getsize(self.file.name) == 0:
+            time.sleep(0.02)
+
+    def mark(self, t0: float, t1: float):
+        self.window = (t0, t1)
+
+    @staticmethod
+    def parse_rows(lines, window=None, slack_s: float = 0.0):
+        """Rows of the sampler's CSV; with a window, only those inside it."""
+        import datetime
+        rows = []
+        for ln in lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            rows.append((ts, parts[1:]))
+        if window is not None:
+            inside = [r for t, r in rows if t is not None and window[0] - slack_s <= t <= window[1] + slack_s]
+            return inside, True
+        return [r for _, r in rows], False
+
+    @staticmethod
+    def summarise(rows, in_window: bool) -> dict:
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        num = lambda s: s.replace(".", "", 1).isdigit()
+        sm = [float(r[1]) for r in rows if num(r[1])]
+        mx = [float(r[2]) for r in rows if num(r[2])]
+        pw = [float(r[3]) for r in rows if num(r[3])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "power_w_max": max(pw) if pw else None,
+                "reasons": reasons, "samples": len(rows),
+                "window": "timed region" if in_window else "warm-up and timed region"}
 
     def stop(self) -> dict:
         if self.proc is None:
@@ -143,21 +234,13 @@ class ClockSampler:
         self.proc.terminate()
         self.proc.wait()
         self.file.flush()
-        rows = []
         with open(self.file.name) as f:
-            for ln in f:
-                parts = [x.strip() for x in ln.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
+            lines = f.readlines()
         os.unlink(self.file.name)
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+        rows, in_window = self.parse_rows(lines, self.window, 1e-3 * self.PERIOD_MS)
+        if not rows:      # a timed region shorter than the sampling period saw no sample
+            rows, in_window = self.parse_rows(lines)
+        return self.summarise(rows, in_window)
 
 
 def measured_hbm_peak():
@@ -278,7 +361,7 @@ def run_reference(args):
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    emit(line)
     return 0
 
 
@@ -701,38 +784,42 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    every = stats_cadence(args.steps)
+    clocks = ClockSampler(dev.index if dev.index is not None else 0)
+    clocks.start()
     for i in range(args.warmup):
         g.step(1, **kw)
-        if (i + 1) % STATS_EVERY == 0:
+        if (i + 1) % every == 0:
             g.stats()
     barrier()
-    # steps run in chunks of STATS_EVERY (one spfm_step call each, so consecutive
+    clocks.wait_live()
+    # steps run in chunks of `every` (one spfm_step call each, so consecutive
     # kernels overlap under programmatic dependent launch); the FP64 stats run
-    # between chunks, inside the timed region but outside the chunk events
+    # after every full chunk, inside the timed region but outside the chunk events
     chunks = []
     left = args.steps
     while left > 0:
-        chunks.append(min(STATS_EVERY, left))
+        chunks.append(min(every, left))
         left -= chunks[-1]
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in chunks]
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(dev.index if dev.index is not None else 0)
-    clocks.start()
     launches = 0
     per_step = g.kernels_per_step()
     stats_seen = []
+    host_t0 = time.time()
     t_start.record(stream)
     for (e0, e1), n in zip(ev, chunks):
         e0.record(stream)
         g.step(n, **kw)
         e1.record(stream)
         launches += per_step * n   # stencil kernel (+ ghost-face kernel unless it writes the images)
-        if n == STATS_EVERY:
+        if n == every:
             stats_seen.append(g.stats())
-            launches += 2
+            launches += 2          # stats kernel + its final reduction
     t_end.record(stream)
     barrier()
+    clocks.mark(host_t0, time.time())
     clk = clocks.stop()
     total_ms = max_over_ranks(t_start.elapsed_time(t_end), ws, dev)
     step_ms = sum(a.elapsed_time(b) for a, b in ev)
@@ -742,12 +829,40 @@ def run_gpu(args):
     peak, peak_kind = measured_hbm_peak()
     achieved = cells * bpu / (avg_kernel_ms / 1e3) / 1e9
     kernel_key = f"spfm_step_kernel_{args.dtype}_27pt_{args.scheme}_{w['nx']}"
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": arm_config(args, w, ws),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
+                     "traffic": profiled_traffic(kernel_key),
+                     "kernel": "spfm_step_kernel", "bytes_per_update": bpu,
+                     "avg_launch_ms": avg_kernel_ms,
+                     "timed": ("stencil kernel, which writes the periodic ghost images itself"
+                               if per_step == 1 else "stencil kernel + ghost-face kernel")
+                              + f"; events around {every}-step chunks"},
+        "clocks": clk, "gpu_launches": launches,
+        # no stats call ran when the timed region had no full chunk
+        "stats_call": ({"ms": (total_ms - step_ms) / len(stats_seen), "calls": len(stats_seen),
+                        "every": every, "note": "interface stats between step chunks, host round trip "
+                                                "included"} if stats_seen else None),
+        "legs": [],
+    }
 
-    # grain anisotropy after the timed run (Sec. 3.3), FP64 on the device
-    grain = g.sphericity(0) if rank == 0 else None
+    def leg(name, result):
+        """One study leg as a line of its own, printed as soon as it is done."""
+        if result is not None and rank == 0:
+            emit({"leg": name, **(result if isinstance(result, dict) else {"result": result})})
+            line["legs"].append(name)
+
+    if rank == 0:
+        leg("last_stats", stats_seen[-1] if stats_seen else None)
+        # grain anisotropy after the timed run (Sec. 3.3), FP64 on the device
+        leg("grain_sphericity", g.sphericity(0))
 
     # the other schemes on the same grid and storage (short timed runs)
-    variants = None
     if rank == 0 and not args.no_variants:
         variants = {}
         for name, sch in (("TI_n", S.SPFM_TI_LOCAL), ("CF+h3", S.SPFM_FD), ("TI_<120>", S.SPFM_TI_GLOBAL)):
@@ -767,31 +882,26 @@ def run_gpu(args):
             variants[name] = {"cell_updates_per_s": cells / (ms / 1e3), "ms_per_step": ms,
                               "frac_hbm": cells * bpu / (ms / 1e3) / 1e9 / peak}
             if sch == S.SPFM_TI_LOCAL:
-                # TI_n is bound by the FP32 pipe: its ceiling from the committed
-                # capture (rate under ncu / FMA-pipe occupancy there)
+                # TI_n is bound by instruction issue: its ceiling from the committed
+                # capture (warp instructions per update at the full issue rate)
                 ceil = profiled_record(f"spfm_step_kernel_{args.dtype}_27pt_local", "alu_ceiling_cell_updates_per_s")
                 variants[name]["bound"] = "alu"
                 variants[name]["alu_ceiling_cell_updates_per_s"] = ceil
                 variants[name]["frac_alu"] = cells / (ms / 1e3) / ceil if ceil else None
+        leg("variants", variants)
 
-    bf16 = None
     if rank == 0 and not args.no_bf16 and args.dtype != "bf16":
-        bf16 = bf16_variant(w, dev)
-    tilted = None
+        leg("bf16_storage", bf16_variant(w, dev))
     if rank == 0 and not args.no_tilted:
-        tilted = tilted_256(dev)
-    relax = None
+        leg("tilted_256", tilted_256(dev))
     if rank == 0 and not args.no_relax:
-        relax = shape_relaxation(dev)
-    friction = None
+        leg("shape_relaxation", shape_relaxation(dev))
     if rank == 0 and not args.no_friction:
-        friction = friction_1d(dev)
-    force_scan = None
+        leg("friction_1d", friction_1d(dev))
     if rank == 0 and not args.no_force_scan:
-        force_scan = force_oscillation()
-    kinetic = None
+        leg("force_oscillation", force_oscillation())
     if rank == 0 and not args.no_kinetic:
-        kinetic = kinetic_anisotropy(dev)
+        leg("kinetic_anisotropy", kinetic_anisotropy(dev))
 
     # end to end through the public API from pinned host memory: upload the
     # initial field, E2E_STEPS steps, stats, read the field back
@@ -817,13 +927,12 @@ def run_gpu(args):
         e2e = {"value": replica_value(cells, E2E_STEPS * iters, ws, e_ms), "unit": UNIT,
                "h2d_bytes_per_step": fb / E2E_STEPS, "d2h_bytes_per_step": (fb + 96) / E2E_STEPS,
                "note": f"per call: host field in, {E2E_STEPS} steps, stats, host field out"}
+    line["e2e"] = e2e
 
-    batched = None
     if rank == 0 and not args.no_batch:
-        batched = batched_vs_plain(args.sweep_grids, dev)
-    serving = None
+        leg("batched", batched_vs_plain(args.sweep_grids, dev))
     if rank == 0 and not args.no_serve:
-        serving = serving_run(args.serve_jobs)
+        leg("serving", serving_run(args.serve_jobs))
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -831,28 +940,9 @@ def run_gpu(args):
         cpu = {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                "sample": f"3 FP64 oracle steps on a {w['nx']}x{w['ny']}x{nzs} z-slab of the "
                          f"workload ({dt:.1f} s)"}
+    line["cpu_baseline"] = cpu
     if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-            "config": arm_config(args, w, ws),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": peak_kind,
-                         "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
-                         "traffic": profiled_traffic(kernel_key),
-                         "kernel": "spfm_step_kernel", "bytes_per_update": bpu,
-                         "avg_launch_ms": avg_kernel_ms,
-                         "timed": ("per step: stencil kernel, which writes the periodic ghost images itself"
-                                   if per_step == 1 else "per step: stencil kernel + ghost-face kernel")
-                                  + " (events around 50-step chunks)"},
-            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
-            "batched": batched, "serving": serving, "grain_sphericity": grain, "variants": variants, "bf16_storage": bf16, "tilted_256": tilted, "shape_relaxation": relax, "friction_1d": friction, "force_oscillation": force_scan, "kinetic_anisotropy": kinetic,
-            "last_stats": stats_seen[-1] if stats_seen else None,
-            "stats_call": {"ms": (total_ms - step_ms) / max(1, len(stats_seen)), "every": STATS_EVERY,
-                           "note": "interface stats between step chunks, host round trip included"},
-        }
-        print(json.dumps(line), flush=True)
+        emit(headline(line))
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -886,8 +976,8 @@ def batch_only(n_grids: int):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / 64
         b.close()
-    print(json.dumps({"workload": f"orientation_sweep_{n_grids}grids_f32_27pt", "cells": cells,
-                      "ms_per_step": ms, "cell_updates_per_s": cells / (ms / 1e3)}), flush=True)
+    emit({"workload": f"orientation_sweep_{n_grids}grids_f32_27pt", "cells": cells,
+          "ms_per_step": ms, "cell_updates_per_s": cells / (ms / 1e3)})
     return 0
 
 
