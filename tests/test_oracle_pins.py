@@ -389,6 +389,47 @@ def test_sphericity_of_ideal_sphere_small():
     assert s["eps_eff"] < 5e-3
 
 
+def test_sphericity_barycentre_is_the_particles():
+    """Sec. 3.3: the radii are taken from the particle's barycentre.  An
+    off-centre sphere in a box that is not a cube separates the particle-weighted
+    barycentre (the sphere's centre) from the matrix-weighted one (near the box
+    centre), so weighting by the wrong phase fails here; the particle may be
+    either phase."""
+    shape, ctr, R, lam = (40, 32, 28), np.array([10.3, 14.1, 12.7]), 6.0, 2.0
+    p = O.Params(*shape, lam=lam)
+    grain0 = O.init_sphere(p, ctr, R)            # phi = 0 inside
+    for phi, inside in ((grain0, 0), (1.0 - grain0, 1)):
+        s = O.sphericity(p, phi, inside_phase=inside)
+        # the profile is radial about ctr: its grid-sampled centroid sits on ctr
+        # up to the aliasing of the sampled profile (2.5e-5 cells at lambda = 2)
+        assert np.abs(np.array(s["barycentre"]) - ctr).max() < 1e-4, s["barycentre"]
+        assert abs(s["R_mean"] - R) < 0.03 and s["eps_eff"] < 5e-3
+        assert s["n_points"] > 300
+    # the matrix weighting would put the centre far from the sphere
+    wrong = O.sphericity(p, grain0, inside_phase=1)
+    assert np.abs(np.array(wrong["barycentre"]) - ctr).max() > 2.0
+    assert wrong["eps_eff"] > 0.2
+
+
+def test_sphericity_of_a_cube_start():
+    """The cube start of Sec. 3.3 (half side h, centre on a grid point, off the
+    box centre): its barycentre is the cube's centre by symmetry, the smallest
+    radius is h exactly (contour points at the face centres, where the profile
+    is the 1D profile of Eq. 3 and the nonlinear interpolation is exact), and the
+    largest is that of the corner of the phi = 1/2 level set, below sqrt(3) h."""
+    ctr, h, lam = np.array([12.0, 11.0, 10.0]), 5.5, 1.0
+    p = O.Params(30, 26, 24, lam=lam)
+    s = O.sphericity(p, O.init_cube(p, ctr, h), inside_phase=0)
+    assert np.abs(np.array(s["barycentre"]) - ctr).max() < 1e-9
+    assert abs(s["R_min"] - h) < 1e-8
+    # on the body diagonal the three 1D fractions are equal: ((1 - t)/2)^3 = 1/2
+    t = 1.0 - 2.0 * 2.0 ** (-1.0 / 3.0)
+    d_corner = h + 0.5 * lam * math.atanh(t)
+    assert math.sqrt(3.0) * d_corner - 0.5 < s["R_max"] < math.sqrt(3.0) * h
+    assert s["eps_eff"] == pytest.approx((s["R_max"] - s["R_min"]) / (2.0 * s["R_mean"]), rel=1e-12)
+    assert s["eps_eff"] > 0.1
+
+
 # ------------------------------------------------------------- reductions
 
 
@@ -490,6 +531,57 @@ def test_local_normal_equals_global_on_planar_profile():
         assert np.abs(Rl - Rg)[ok].max() < 1e-11
         if (~ok).any():
             assert np.abs(Rl - Rg)[~ok].max() < 1e-4
+
+
+def test_local_normal_fallback_is_the_cf_potential():
+    """Reading r14, cells with no normal: where |grad psi| < 1e-8 (a uniform
+    field, or a cell whose six face neighbours sit in the clamp on the same
+    side) the cell takes the CF potential.  A uniform phi = 0.3 field then moves
+    at the closed-form CF rate R = -(16 D / lambda^2) q s - (4 M dF/(lambda Gamma)) q
+    with D = 2M/(3 C_Gamma); the other reading, a_k = 0, would leave only the
+    driving term."""
+    for stencil in (6, 18, 26):
+        M, Gamma, lam, dF, Cg = 0.7, 1.3, 2.5, 0.04, 2.0 / 3.0
+        p = O.Params(6, 5, 4, lam=lam, M=M, Gamma=Gamma, dF=dF, stencil=stencil, scheme=O.TI_LOCAL,
+                     n=tuple(_unit([1.0, 2.0, 3.0])))
+        phi0 = 0.3
+        R, _ = O.rhs(p, np.full(p.shape, phi0))
+        q, s, D = phi0 * (1 - phi0), 1 - 2 * phi0, 2 * M / (3 * Cg)
+        expect = -(16.0 * D / lam ** 2) * q * s - 4 * M * dF / (lam * Gamma) * q
+        assert np.abs(R - expect).max() < 1e-14
+        assert abs(expect + 4 * M * dF / (lam * Gamma) * q) > 0.1     # a_k = 0 differs
+
+
+def test_local_normal_fallback_cells_in_the_clamp():
+    """A planar profile with a bulk perturbation: cells whose psi differences are
+    exactly zero on all three axes (all face neighbours in the same clamp) take
+    the CF right-hand side, every other cell the TI right-hand side with the
+    normal estimated from psi; the mask is rebuilt here from the clamp rule."""
+    n = _unit([1.0, 0.3, 0.0])
+    p = O.Params(40, 8, 6, bc=(O.NOFLUX, O.NOFLUX) + (O.PERIODIC,) * 4, n=tuple(n), lam=2.0, dF=0.02,
+                 stencil=26, scheme=O.TI_LOCAL)
+    phi = O.init_planar(p, float(n @ [19.5, 3.5, 2.5]))
+    # bulk cells perturbed inside the clamp (phi < 1e-6 and 1 - phi < 1e-6)
+    rng = np.random.default_rng(9)
+    lo, hi = phi < 1e-9, phi > 1 - 1e-9
+    phi[lo] = 1e-7 * rng.random(lo.sum())
+    phi[hi] = 1 - 1e-7 * rng.random(hi.sum())
+    Rl, _ = O.rhs(p, phi)
+    Rcf, _ = O.rhs(O.Params(**{**p.__dict__, "scheme": O.CF}), phi)
+    pad = O.fill_ghosts(p, phi)
+    psi = 0.5 * p.lam * np.arctanh(1 - 2 * np.clip(pad, 1e-6, 1 - 1e-6))
+    g2 = np.zeros(p.shape)
+    for ax in range(3):
+        sp, sm = [slice(1, -1)] * 3, [slice(1, -1)] * 3
+        sp[2 - ax], sm[2 - ax] = slice(2, None), slice(0, -2)
+        g2 += ((psi[tuple(sp)] - psi[tuple(sm)]) / (2 * p.dx)) ** 2
+    fb = ~(np.sqrt(g2) >= 1e-8)
+    assert fb.sum() > 100 and (~fb).sum() > 100
+    assert np.array_equal(Rl[fb], Rcf[fb])
+    assert (lo & fb).sum() > 10 and (hi & fb).sum() > 10
+    # elsewhere the RHS is not the CF one: the interface cells see the TI potential
+    band = (phi > 0.05) & (phi < 0.95)
+    assert np.abs(Rl - Rcf)[band].max() > 1e-3
 
 
 # ------------------------------------------------ constant-volume relaxation
