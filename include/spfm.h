@@ -181,9 +181,11 @@ spfm_status spfm_interface_stats(spfm_grid *g, int flags, spfm_stats *out);
  * define the profile inversion.  out->energy is NaN, steps and time are 0.
  * The reduction partials sit in a fixed array inside the library, sized for
  * nz <= 1024 (96 KiB, held by every GPU that loads the library until exit):
- * larger nz returns SPFM_EINVAL.  The first call on a device looks up the
- * array's address; make it before any stream capture.  Calls share the array,
- * so calls that overlap on the GPU race.  Synchronises desc->stream. */
+ * larger nz returns SPFM_EINVAL, as do the extent limits of spfm_create_grid
+ * and |n| != 1.  The first call on a device looks up the array's address for
+ * the current device; make it before any stream capture.  desc->stream must
+ * belong to the current device (else SPFM_EINVAL).  Calls share the array, so
+ * calls that overlap on the GPU race.  Synchronises desc->stream. */
 spfm_status spfm_interface_stats_static(const spfm_grid_desc *desc, const void *field, double lambda,
                                         double dx, spfm_stats *out);
 

@@ -246,6 +246,16 @@ void stats_from_reduction(const spfm_grid *g, const double *h, int energy, spfm_
     out->time = g->time;
 }
 
+int check_extent(const spfm_grid_desc *d, size_t px, const char *who)
+{
+    if ((long long)(d->nx + 2) * (d->ny + 2) >= (1LL << 30) || (long long)(d->nx + 2) * d->nz >= (1LL << 30) ||
+        (long long)d->ny * d->nz >= (1LL << 30))
+        return fail(nullptr, SPFM_EINVAL, "%s: a face of the grid exceeds 2^30 cells", who);
+    if ((long long)px * (d->ny + 2) * (long long)(d->nz + 2) >= (1LL << 40))
+        return fail(nullptr, SPFM_EINVAL, "%s: grid too large", who);
+    return SPFM_OK;
+}
+
 }  // namespace spfm_host
 
 using namespace spfm_host;
@@ -281,11 +291,8 @@ spfm_status spfm_create_grid(const spfm_grid_desc *d, spfm_grid **out)
     size_t px = 0, off = 0, fb = 0, sb = 0;
     spfm_status st = spfm_layout(d, &px, &off, &fb, &sb);
     if (st != SPFM_OK) return st;
-    if ((long long)(d->nx + 2) * (d->ny + 2) >= (1LL << 30) || (long long)(d->nx + 2) * d->nz >= (1LL << 30) ||
-        (long long)d->ny * d->nz >= (1LL << 30))
-        return fail(nullptr, SPFM_EINVAL, "spfm_create_grid: a face of the grid exceeds 2^30 cells");
-    if ((long long)px * (d->ny + 2) * (long long)(d->nz + 2) >= (1LL << 40))
-        return fail(nullptr, SPFM_EINVAL, "spfm_create_grid: grid too large");
+    st = check_extent(d, px, "spfm_create_grid");
+    if (st != SPFM_OK) return st;
     for (int f = 0; f < 6; ++f)
         if (d->bc[f] != SPFM_PERIODIC && d->bc[f] != SPFM_NOFLUX && d->bc[f] != SPFM_CONTACT)
             return fail(nullptr, SPFM_EINVAL, "spfm_create_grid: bad boundary kind on face %d", f);

@@ -29,6 +29,10 @@ int fail(spfm_grid *g, int code, const char *fmt, ...);
 int cuda_fail(spfm_grid *g, cudaError_t e, const char *what);
 void set_thread_error(const char *msg);
 size_t elem_size(int dtype);
+// Extent limits of a grid (every face below 2^30 cells, the padded field below
+// 2^40 elements): 0 when they hold, else SPFM_EINVAL with the thread's message
+// set (prefixed by `who`).
+int check_extent(const spfm_grid_desc *d, size_t pitch_x, const char *who);
 
 // Model coefficients in FP64 (a1).  gamma defaults, nu_j = 3/m_j, c_j, A_k
 // grouped by value, stability and phase checks.

@@ -11,7 +11,9 @@
 //
 // The first call on a device resolves the array's device address with
 // cudaGetSymbolAddress (host code cannot use the array's name as a device
-// address); make that first call before any stream capture begins.
+// address); make that first call before any stream capture begins.  The
+// address is that of the current device, so desc->stream must belong to the
+// current device (a stream of another device is refused with SPFM_EINVAL).
 // One CTA reduces one z plane into its slot of the array, then one CTA sums
 // the slots in plane order, so the result is reproducible.  Every slot that is
 // read was written by the same call, so nothing has to be cleared between
@@ -154,12 +156,29 @@ extern "C" spfm_status spfm_interface_stats_static(const spfm_grid_desc *desc, c
     size_t px = 0, off = 0;
     spfm_status st = spfm_layout(desc, &px, &off, nullptr, nullptr);
     if (st != SPFM_OK) return st;
+    st = spfm_host::check_extent(desc, px, "spfm_interface_stats_static");
+    if (st != SPFM_OK) return st;
+    const double nn = desc->n[0] * desc->n[0] + desc->n[1] * desc->n[1] + desc->n[2] * desc->n[2];
+    if (!(fabs(nn - 1.0) < 1e-9))
+        return fail(nullptr, SPFM_EINVAL, "spfm_interface_stats_static: |n| = %g, must be 1", sqrt(nn));
     if (desc->nz > kStaticPlanes)
         return fail(nullptr, SPFM_EINVAL,
                     "spfm_interface_stats_static: nz = %d exceeds the %d planes its fixed scratch holds",
                     desc->nz, kStaticPlanes);
     if ((uintptr_t)field & 15)
         return fail(nullptr, SPFM_EINVAL, "spfm_interface_stats_static: field not 16-byte aligned");
+    // the array's address is resolved for the current device, so the stream
+    // must belong to that device
+    cudaStream_t s = (cudaStream_t)desc->stream;
+    int cur_dev = -1, stream_dev = -1;
+    cudaError_t de = cudaGetDevice(&cur_dev);
+    if (de == cudaSuccess) de = cudaStreamGetDevice(s, &stream_dev);
+    if (de != cudaSuccess)
+        return fail(nullptr, SPFM_ECUDA, "spfm_interface_stats_static: %s", cudaGetErrorString(de));
+    if (stream_dev != cur_dev)
+        return fail(nullptr, SPFM_EINVAL,
+                    "spfm_interface_stats_static: desc->stream belongs to device %d, the current device is %d",
+                    stream_dev, cur_dev);
     int code = 0;
     double *scratch = static_scratch_address(&code);
     if (!scratch)
@@ -176,7 +195,6 @@ extern "C" spfm_status spfm_interface_stats_static(const spfm_grid_desc *desc, c
     for (int i = 0; i < 3; ++i) { a.n[i] = desc->n[i]; a.ctr[i] = desc->center[i]; }
     a.lambda = lambda;
     a.dx = dx;
-    cudaStream_t s = (cudaStream_t)desc->stream;
     if (desc->dtype == SPFM_F64) plane_stats_kernel<double><<<desc->nz, 256, 0, s>>>(a, (const double *)field, scratch);
     else if (desc->dtype == SPFM_F32) plane_stats_kernel<float><<<desc->nz, 256, 0, s>>>(a, (const float *)field, scratch);
     else plane_stats_kernel<__nv_bfloat16><<<desc->nz, 256, 0, s>>>(a, (const __nv_bfloat16 *)field, scratch);

@@ -3,7 +3,17 @@ R = 37.5, lambda = 3, dF = 0.08 (the same R/R* as R = 150 at dF = 0.02),
 periodic, 27-point, dt = 0.05.  FP32 on the GPU against the FP64 oracle on the
 same start: the field within 2e-5 and the radial velocity dR/dt of the radius
 estimator (Sec. 2.3 inversion, radial form) within 1e-4 relative.
+
+Horizons: TI_<120> over the workload's full 10000 steps (velocity over the last
+1000); TI_n over 2000 (velocity over the last 1000): its oracle runs at about
+a third of the TI_<120> rate, and 10000 steps would hold the test for some
+five minutes of host time.
+
+Set SPFM_RECORD=<file> to append the measured errors as a JSON line.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -22,8 +32,8 @@ def _lib():
     S.load()
 
 
-@pytest.mark.parametrize("scheme,oscheme,n1,n2", [(S.SPFM_TI_GLOBAL, O.TI_GLOBAL, 200, 200),
-                                                  (S.SPFM_TI_LOCAL, O.TI_LOCAL, 100, 100)])
+@pytest.mark.parametrize("scheme,oscheme,n1,n2", [(S.SPFM_TI_GLOBAL, O.TI_GLOBAL, 9000, 1000),
+                                                  (S.SPFM_TI_LOCAL, O.TI_LOCAL, 1000, 1000)])
 def test_grain_replica_field_and_velocity(scheme, oscheme, n1, n2):
     w = WL.sphere_replica_128cubed()
     N, ctr, R = w["nx"], w["ctr"], w["R"]
@@ -44,9 +54,15 @@ def test_grain_replica_field_and_velocity(scheme, oscheme, n1, n2):
     phi = O.step(p, phi, n2)
     r2o = O.stats(p, phi, ctr)["radius"]
 
-    err = np.abs(g.get_field(to_host=True).double().numpy() - phi).max()
-    assert err <= 2e-5, err
+    err = float(np.abs(g.get_field(to_host=True).double().numpy() - phi).max())
     T = n2 * w["dt"]
     v, vo = (r2 - r1) / T, (r2o - r1o) / T
+    path = os.environ.get("SPFM_RECORD")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps({"workload": "sphere_replica_128", "scheme": "TI_n" if oscheme == O.TI_LOCAL
+                                else "TI_<120>", "dtype": "f32", "steps": n1 + n2, "field_err": err,
+                                "vel_err_vs_oracle": abs(v / vo - 1.0), "radius": r2}) + "\n")
+    assert err <= 2e-5, err
     assert vo > 0.0                       # the grain grows: dF beats the curvature term
     assert abs(v / vo - 1.0) < 1e-4, (v, vo)
