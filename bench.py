@@ -87,6 +87,8 @@ def parse(argv=None):
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64", "bf16"])
     ap.add_argument("--scheme", default="ti120", choices=["ti120", "fd", "local"])
+    ap.add_argument("--rounding", default="nearest", choices=["nearest", "stochastic"],
+                    help="rounding of the update of the timed grid (FP32/BF16)")
     ap.add_argument("--no-variants", action="store_true", help="skip the TI_n / CF timings")
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-storage leg")
     ap.add_argument("--no-relax", action="store_true", help="skip the constant-volume shape relaxation")
@@ -101,6 +103,9 @@ def parse(argv=None):
     ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
     ap.add_argument("--serve-jobs", type=int, default=2000)
     ap.add_argument("--sweep-grids", type=int, default=256)
+    ap.add_argument("--tilted-only", action="store_true",
+                    help="only the 256^3 tilted plane with contact faces (FP32 TI_<111>): 5 + 50 steps, "
+                         "its step rate (a small command to profile the contact-face path)")
     ap.add_argument("--batch-only", action="store_true",
                     help="only the batched sweep: build it, 32 + 64 steps, print its rate (a small "
                          "command to profile the batch kernel)")
@@ -124,7 +129,8 @@ SCHEME_NAME = {"ti120": "TI_<120>", "fd": "CF+h3", "local": "TI_n"}
 def arm_config(args, w, ws):
     """The `config` of the JSON line, the same for the GPU arm and the oracle arm."""
     cells = w["nx"] * w["ny"] * w["nz"]
-    return {"workload": w["name"] + f"_{args.scheme}_{args.dtype}_27pt",
+    sr = "_sr" if getattr(args, "rounding", "nearest") == "stochastic" else ""
+    return {"workload": w["name"] + f"_{args.scheme}_{args.dtype}{sr}_27pt",
             "grid": [w["nx"], w["ny"], w["nz"]], "stencil": 27, "scheme": SCHEME_NAME[args.scheme],
             "lambda": w["lam"], "dt": w["dt"], "dF": w["dF"], "bc": "periodic",
             "stats_every": stats_cadence(args.steps),
@@ -255,8 +261,9 @@ def measured_hbm_peak():
 
 # the sources that decide the stencil kernel's code (its traffic record is
 # dropped as soon as one of them changes)
-STEP_SOURCES = ("spfm_internal.h", "step_kernel.cuh", "step_f32.cu", "step_f64.cu", "step_bf16.cu",
+STEP_SOURCES = ("spfm_internal.h", "step_kernel.cuh", "tiles.h", "step_f32.cu", "step_f64.cu", "step_bf16.cu",
                 "step_f32_img.cu", "step_f64_img.cu", "step_bf16_img.cu")
+TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic.json")
 
 
 def source_hash(names=STEP_SOURCES):
@@ -272,9 +279,8 @@ def source_hash(names=STEP_SOURCES):
 def profiled_record(kernel_key: str, field: str):
     """A figure of the committed ncu summaries (profiles/traffic.json), only
     while the kernel sources are unchanged since the capture."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        with open(path) as f:
+        with open(TRAFFIC_PATH) as f:
             d = json.load(f)
     except (OSError, ValueError):
         return None
@@ -368,22 +374,26 @@ def run_reference(args):
 # --------------------------------------------------------------------- GPU arm
 
 
-def batched_vs_plain(n_grids: int, dev):
+def batched_vs_plain(n_grids: int, dev, rounding=None):
     """Orientation sweep: n_grids uneven grids (edges 32..96, random normals,
-    lambda/dx in {2,3,4,6}), FP32, 27-point TI with each grid's own n.  Times
-    the batched path (one persistent launch per step, graph replay) against the
-    plain path (spfm_step per grid per step) and measures each grid's velocity
-    over steps 1000..2000 of the batched run against v_th = -M dF/Gamma."""
+    lambda/dx in {2,3,4,6}), FP32 with stochastic rounding of the update,
+    27-point TI with each grid's own n.  Times the batched path (one persistent
+    launch per step, graph replay) against the plain path (spfm_step per grid
+    per step; the same arithmetic, bit for bit) and measures each grid's
+    velocity over steps 1000..2000 of the batched run against
+    v_th = -M dF/Gamma."""
     import torch
     from paper_1910_05180_gb300 import spfm as S
     from paper_1910_05180_gb300 import workloads as WL
+    rounding = S.SPFM_ROUND_STOCHASTIC if rounding is None else rounding
     jobs = WL.orientation_sweep(n_grids=n_grids)
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         grids = []
-        for j in jobs:
+        for i, j in enumerate(jobs):
             g = S.Grid(j["nx"], j["ny"], j["nz"], dtype=S.SPFM_F32, bc=(S.SPFM_CONTACT,) * 6, n=j["n"],
                        stream=stream)
+            g.set_rounding(rounding, seed=i)
             g.init_planar(j["c"], j["lam"])
             grids.append(g)
         args = [S.step_args(lam=j["lam"], dt=j["dt"], dF=j["dF"], stencil=26) for j in jobs]
@@ -423,6 +433,7 @@ def batched_vs_plain(n_grids: int, dev):
         errs = np.array(errs)
         b.close()
     return {"workload": f"orientation_sweep_{n_grids}grids_f32_27pt", "cells": int(cells),
+            "rounding": "stochastic" if rounding == S.SPFM_ROUND_STOCHASTIC else "nearest",
             "plain_cell_updates_per_s": plain, "batched_cell_updates_per_s": batched,
             "speedup": batched / plain, "velocity_rel_err_median": float(np.median(errs)),
             "velocity_rel_err_p90": float(np.percentile(errs, 90)),
@@ -683,8 +694,11 @@ def bf16_variant(w, dev, steps: int = 100):
         n = (1.0 / 3 ** 0.5,) * 3
         shape = (96, 64, 64)
         c = float(np.dot(n, (np.array(shape) - 1) / 2.0))
-        for name, dt_ in (("f32", S.SPFM_F32), ("bf16", S.SPFM_BF16)):
+        for name, dt_, rnd in (("f32", S.SPFM_F32, S.SPFM_ROUND_NEAREST), ("bf16", S.SPFM_BF16, S.SPFM_ROUND_NEAREST),
+                               ("f32_sr", S.SPFM_F32, S.SPFM_ROUND_STOCHASTIC),
+                               ("bf16_sr", S.SPFM_BF16, S.SPFM_ROUND_STOCHASTIC)):
             h = S.Grid(*shape, dtype=dt_, bc=(S.SPFM_CONTACT,) * 6, n=n, stream=stream)
+            h.set_rounding(rnd, seed=3)
             h.init_planar(c, 3.0)
             a = dict(lam=3.0, dt=0.05, dF=0.05, stencil=26, scheme=S.SPFM_TI_GLOBAL)
             h.step(1000, **a)
@@ -695,6 +709,7 @@ def bf16_variant(w, dev, steps: int = 100):
             out[f"planar_velocity_rel_err_{name}"] = abs(v / -0.05 - 1.0)
             h.close()
     out["accepted"] = bool(out["planar_velocity_rel_err_bf16"] <= 1e-4)
+    out["accepted_with_stochastic_rounding"] = bool(out["planar_velocity_rel_err_bf16_sr"] <= 1e-4)
     out["workload"] = w["name"] + "_ti120_bf16_27pt"
     return out
 
@@ -742,15 +757,105 @@ def tilted_256(dev, steps: int = 50, window: int = 400):
     return out
 
 
-def serving_run(n_jobs: int):
-    """Poisson stream (200 jobs/s) of velocity-measurement jobs, edges 32..192,
-    continuous batching under a 120 GB budget, retirement at |dv/v| < 1e-4."""
+def velocity_vs_oracle(dev, n_grids: int = 4, steps: int = 2000, window: int = 1000):
+    """GPU against FP64-oracle velocities on the same jobs: the 32^3 grids of
+    the orientation sweep with the smallest dF (the hardest case for FP32),
+    batched, with round-to-nearest and with stochastic rounding of the update;
+    velocity over the last `window` of `steps` steps.  Errors are relative to
+    v_th = -M dF/Gamma (Sec. 2.1), next to the oracle's own error against it."""
+    import torch
+    import oracle as O
+    from paper_1910_05180_gb300 import spfm as S
     from paper_1910_05180_gb300 import workloads as WL
-    from paper_1910_05180_gb300.serve import GpuBackend, Server, job_from_workload
+    jobs = sorted([j for j in WL.orientation_sweep() if j["nx"] == 32], key=lambda j: j["dF"])[:n_grids]
+    rows = []
+    res = {}
+    stream = torch.cuda.Stream(device=dev)
+    for mode, rounding in (("nearest", S.SPFM_ROUND_NEAREST), ("stochastic", S.SPFM_ROUND_STOCHASTIC)):
+        with torch.cuda.stream(stream):
+            grids = []
+            for i, j in enumerate(jobs):
+                g = S.Grid(j["nx"], j["ny"], j["nz"], dtype=S.SPFM_F32, bc=(S.SPFM_CONTACT,) * 6, n=j["n"],
+                           stream=stream)
+                g.set_rounding(rounding, seed=i)
+                g.init_planar(j["c"], j["lam"])
+                grids.append(g)
+            args = [S.step_args(lam=j["lam"], dt=j["dt"], dF=j["dF"], stencil=26) for j in jobs]
+            b = S.Batch(grids, stream=stream)
+            b.step(steps - window, args)
+            s1 = b.stats()
+            b.step(window, args)
+            s2 = b.stats()
+            res[mode] = [(a2["position"] - a1["position"]) / (window * j["dt"]) for j, a1, a2 in zip(jobs, s1, s2)]
+            b.close()
+            for g in grids:
+                g.close()
+    for i, j in enumerate(jobs):
+        p = O.Params(j["nx"], j["ny"], j["nz"], bc=(O.CONTACT,) * 6, n=j["n"], lam=j["lam"], dt=j["dt"],
+                     dF=j["dF"], stencil=26)
+        phi = O.step(p, O.init_planar(p, j["c"]), steps - window)
+        c1 = O.stats(p, phi)["position"]
+        phi = O.step(p, phi, window)
+        vo = (O.stats(p, phi)["position"] - c1) / (window * j["dt"])
+        v_th = -j["dF"]
+        rows.append({"grid": j["name"], "edge": j["nx"], "lam": j["lam"], "dF": j["dF"],
+                     "oracle_vs_vth": abs(vo / v_th - 1.0),
+                     "nearest_vs_oracle": abs(res["nearest"][i] - vo) / abs(v_th),
+                     "stochastic_vs_oracle": abs(res["stochastic"][i] - vo) / abs(v_th)})
+    return {"workload": f"orientation_sweep_32cubed_smallest_dF_{steps}steps_f32_27pt", "rows": rows}
+
+
+def rounding_cost(w, dev, steps: int = 100):
+    """Step time of the default workload with stochastic rounding of the update
+    against round to nearest (the same grid and steps)."""
+    import torch
+    from paper_1910_05180_gb300 import spfm as S
+    stream = torch.cuda.Stream(device=dev)
+    out = {}
+    cells = w["nx"] * w["ny"] * w["nz"]
+    with torch.cuda.stream(stream):
+        g = S.Grid(w["nx"], w["ny"], w["nz"], dtype=S.SPFM_F32, bc=(S.SPFM_PERIODIC,) * 6, n=w["u"],
+                   center=w["ctr"], stream=stream)
+        kw = dict(lam=w["lam"], dx=w["dx"], dt=w["dt"], dF=w["dF"], stencil=26, scheme=S.SPFM_TI_GLOBAL)
+        for mode, rounding in (("nearest", S.SPFM_ROUND_NEAREST), ("stochastic", S.SPFM_ROUND_STOCHASTIC)):
+            g.set_rounding(rounding, seed=1)
+            g.init_sphere(w["ctr"], w["R"], w["lam"], w["dx"])
+            g.step(5, **kw)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            g.step(steps, **kw)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / steps
+            out[mode] = {"ms_per_step": ms, "cell_updates_per_s": cells / (ms / 1e3)}
+        g.close()
+    out["cost"] = out["stochastic"]["ms_per_step"] / out["nearest"]["ms_per_step"] - 1.0
+    out["workload"] = w["name"] + "_ti120_f32_27pt"
+    return out
+
+
+def serving_run(n_jobs: int, n_plain: int = 200):
+    """Poisson stream (200 jobs/s) of velocity-measurement jobs, edges 32..192,
+    FP32 with stochastic rounding, continuous batching under a 120 GB budget,
+    retirement at |dv/v| < 1e-4.  Then the first n_plain jobs of the same
+    stream twice: served, and through the one-launch-per-job path (the same
+    windows and retirement, each job stepped and measured on its own); their
+    rates give served / plain."""
+    from paper_1910_05180_gb300 import workloads as WL
+    from paper_1910_05180_gb300.serve import GpuBackend, PlainGpuBackend, Server, job_from_workload
     jobs = [job_from_workload(w) for w in WL.serving_stream(n_jobs=n_jobs)]
     srv = Server(GpuBackend(), hbm_budget=120e9, window=200, tol=1e-4, max_steps=20000)
     out = srv.run(jobs)
-    out["workload"] = f"poisson200hz_{n_jobs}jobs_edge32-192_f32_27pt"
+    out["workload"] = f"poisson200hz_{n_jobs}jobs_edge32-192_f32_sr_27pt"
+    if n_plain:
+        sub = jobs[:n_plain]
+        a = Server(GpuBackend(), hbm_budget=120e9, window=200, tol=1e-4, max_steps=20000).run(sub)
+        b_srv = Server(PlainGpuBackend(), hbm_budget=120e9, window=200, tol=1e-4, max_steps=20000)
+        b = b_srv.run(sub)
+        keep = ("wall_s", "cell_updates", "cell_updates_per_s", "latency_p50_s", "latency_p99_s", "converged")
+        out["vs_plain"] = {"jobs": n_plain, "served": {k: a[k] for k in keep}, "plain": {k: b[k] for k in keep},
+                           "speedup": a["cell_updates_per_s"] / b["cell_updates_per_s"]}
     return out
 
 
@@ -773,6 +878,8 @@ def run_gpu(args):
     with torch.cuda.stream(stream):
         g = S.Grid(w["nx"], w["ny"], w["nz"], dtype=dtype, bc=(S.SPFM_PERIODIC,) * 6, n=w["u"],
                    center=w["ctr"], stream=stream)
+        if args.rounding == "stochastic":
+            g.set_rounding(S.SPFM_ROUND_STOCHASTIC, seed=1)
         g.init_sphere(w["ctr"], w["R"], w["lam"], w["dx"])
     kw = dict(M=w["M"], Gamma=w["Gamma"], lam=w["lam"], dx=w["dx"], dt=w["dt"], dF=w["dF"],
               stencil=w["stencil"], scheme=scheme)
@@ -890,6 +997,8 @@ def run_gpu(args):
                 variants[name]["frac_alu"] = cells / (ms / 1e3) / ceil if ceil else None
         leg("variants", variants)
 
+    if rank == 0 and not args.no_variants and args.dtype == "f32":
+        leg("stochastic_rounding_cost", rounding_cost(w, dev))
     if rank == 0 and not args.no_bf16 and args.dtype != "bf16":
         leg("bf16_storage", bf16_variant(w, dev))
     if rank == 0 and not args.no_tilted:
@@ -933,6 +1042,8 @@ def run_gpu(args):
         leg("batched", batched_vs_plain(args.sweep_grids, dev))
     if rank == 0 and not args.no_serve:
         leg("serving", serving_run(args.serve_jobs))
+    if rank == 0 and not args.no_batch:
+        leg("velocity_vs_oracle", velocity_vs_oracle(dev))
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -981,10 +1092,43 @@ def batch_only(n_grids: int):
     return 0
 
 
+def tilted_only(args):
+    """The 256^3 tilted plane (n || [111], contact faces, lambda = 3) alone in
+    FP32 storage with the TI_<111> step: 5 warm-up steps, then 50 timed; prints
+    one JSON line."""
+    import torch
+    from paper_1910_05180_gb300 import spfm as S
+    from paper_1910_05180_gb300 import workloads as WL
+    w = WL.tilted_111_256cubed()[1]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        g = S.Grid(w["nx"], w["ny"], w["nz"], dtype=S.SPFM_F32, bc=(S.SPFM_CONTACT,) * 6, n=w["n"], stream=stream)
+        if args.rounding == "stochastic":
+            g.set_rounding(S.SPFM_ROUND_STOCHASTIC, seed=1)
+        g.init_planar(w["c"], w["lam"], w["dx"])
+        kw = dict(lam=w["lam"], dx=w["dx"], dt=w["dt"], dF=w["dF"], stencil=26)
+        g.step(5, **kw)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        g.step(50, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 50
+    cells = w["nx"] * w["ny"] * w["nz"]
+    peak, _ = measured_hbm_peak()
+    emit({"workload": w["name"] + "_contact_ti111_f32_27pt", "ms_per_step": ms,
+          "cell_updates_per_s": cells / (ms / 1e3), "frac_hbm": cells * 8 / (ms / 1e3) / 1e9 / peak,
+          "kernels_per_step": g.kernels_per_step()})
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.tilted_only:
+        return tilted_only(args)
     if args.batch_only:
         return batch_only(args.sweep_grids)
     return run_gpu(args)

@@ -68,6 +68,7 @@ enum { SPFM_PERIODIC = 0, SPFM_NOFLUX = 1, SPFM_CONTACT = 2 };   /* boundary kin
  * h_Abel = phi^2 / (phi^2 + (1 - phi)^2) */
 enum { SPFM_TI_GLOBAL = 0, SPFM_TI_LOCAL = 1, SPFM_FD = 2, SPFM_FD_H5 = 3, SPFM_FD_HABEL = 4 };
 enum { SPFM_STATS_ENERGY = 1 };                                  /* stats flags */
+enum { SPFM_ROUND_NEAREST = 0, SPFM_ROUND_STOCHASTIC = 1 };      /* update rounding */
 
 typedef struct spfm_grid spfm_grid;
 typedef struct spfm_batch spfm_batch;
@@ -124,6 +125,29 @@ spfm_status spfm_layout(const spfm_grid_desc *desc, size_t *pitch_x, size_t *x_o
 spfm_status spfm_create_grid(const spfm_grid_desc *desc, spfm_grid **out);
 spfm_status spfm_destroy_grid(spfm_grid *g);
 spfm_status spfm_set_stream(spfm_grid *g, void *stream);
+
+/* Rounding of the explicit update phi + dt R (Eq. 2) to the storage type.
+ * SPFM_ROUND_NEAREST (the default) rounds to nearest.  SPFM_ROUND_STOCHASTIC
+ * rounds up or down with probabilities proportional to the distances (the
+ * expected stored value is the exact update; an exactly representable update
+ * is stored as is): with FP32 or BF16 storage, a slow interface moves by less
+ * than half a unit in the last place of phi near phi = 1 each step, and
+ * round-to-nearest drops those increments, which biases its velocity (about
+ * 2e-4 relative at dF = 3e-4 and 3e-3 at dF = 1e-4 in FP32, lambda = 2..6,
+ * dt = 0.05).  The random bits are a hash of the padded cell index and a key
+ * of (seed, the grid's step count), so a run is reproducible and a grid
+ * draws the same bits alone and in a batch.  FP64 grids: SPFM_EINVAL (their
+ * increments are not lost).  Takes effect at the next step; all grids of a
+ * batch must share the mode.  Costs about 11 instructions per cell update. */
+spfm_status spfm_set_rounding(spfm_grid *g, int mode, unsigned long long seed);
+
+/* Test hook of the failure reporting (the paper has no counterpart): the next
+ * spfm_step launch skips the copy of one plane in its first CTA, whose bounded
+ * waits (about 2 s each) then give up; the kernel returns without writing that
+ * tile, and the next spfm_interface_stats reports SPFM_ETIMEOUT.  The field is
+ * invalid afterwards: re-initialise it (init or set_field clears the error).
+ * One-shot; no effect on batches. */
+spfm_status spfm_debug_skip_copy(spfm_grid *g);
 
 /* Ideal planar profile of Eq. 3, phi = (1 - tanh(2 (p.n - c)/lambda))/2 at
  * p = dx (i, j, k), with the desc's n.  Computed in FP64, stored in dtype. */

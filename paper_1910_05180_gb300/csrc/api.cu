@@ -342,6 +342,25 @@ spfm_status spfm_set_stream(spfm_grid *g, void *stream)
     return SPFM_OK;
 }
 
+spfm_status spfm_debug_skip_copy(spfm_grid *g)
+{
+    if (!g) return fail(nullptr, SPFM_EINVAL, "spfm_debug_skip_copy: grid is NULL");
+    g->skip_copy = true;
+    return SPFM_OK;
+}
+
+spfm_status spfm_set_rounding(spfm_grid *g, int mode, unsigned long long seed)
+{
+    if (!g) return fail(nullptr, SPFM_EINVAL, "spfm_set_rounding: grid is NULL");
+    if (mode != SPFM_ROUND_NEAREST && mode != SPFM_ROUND_STOCHASTIC)
+        return fail(g, SPFM_EINVAL, "spfm_set_rounding: unknown mode %d", mode);
+    if (mode == SPFM_ROUND_STOCHASTIC && g->d.dtype == SPFM_F64)
+        return fail(g, SPFM_EINVAL, "spfm_set_rounding: stochastic rounding is for FP32 and BF16 storage");
+    g->rounding = mode;
+    g->sr_seed = sr_seed_mix(seed);
+    return SPFM_OK;
+}
+
 int spfm_current(const spfm_grid *g) { return g ? g->cur : -1; }
 
 int spfm_kernels_per_step(const spfm_grid *g) { return g ? (writes_own_images(g) ? 1 : 2) : -1; }
@@ -415,7 +434,11 @@ spfm_status spfm_step(spfm_grid *g, int n_steps, double M, double Gamma, double 
     // all faces periodic and rows of whole 32-byte sectors: each step writes the
     // periodic images of its new cells, and no face kernel runs between steps
     const bool images = writes_own_images(g);
-    auto mode_of = [&](int i) { return images ? kWaitAll | kImages : (i == 0 ? kWaitAll : kWaitFaces); };
+    const int skip = g->skip_copy && n_steps > 0 ? kSkipCopy : 0;
+    g->skip_copy = g->skip_copy && n_steps == 0;
+    auto mode_of = [&](int i) {
+        return (images ? kWaitAll | kImages : (i == 0 ? kWaitAll : kWaitFaces)) | (i == 0 ? skip : 0);
+    };
     int *err = err_word(g);
     if (g->d.dtype == SPFM_F64) {
         StepCoef<double> c;
@@ -435,8 +458,11 @@ spfm_status spfm_step(spfm_grid *g, int n_steps, double M, double Gamma, double 
         StepCoef<float> c;
         fill_coef<float>(g, m, dt, stencil, c);
         set_local_coef<float>(c, lambda, dx);
+        cfg.rounding = g->rounding;
         for (int i = 0; i < n_steps; ++i) {
             cfg.mode = mode_of(i);
+            // the step's key of the stochastic rounding: seed and the grid's step count
+            c.sr_key = sr_step_key(g->sr_seed, g->steps + i);
             cudaError_t e;
             if (g->d.dtype == SPFM_F32)
                 e = launch_step_f32(c, (const float *)g->d.field[g->cur], (float *)g->d.field[1 - g->cur],

@@ -30,7 +30,7 @@ constexpr int kMinDepth = 8;
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
-    size_t grids, items, ghosts, stats_jobs, partials, finals, err, total;
+    size_t grids, items, ghosts, stats_jobs, partials, finals, err, steps, total;
 };
 
 size_t grid_record_bytes(int dtype)
@@ -78,6 +78,8 @@ Layout layout_for(int dtype, int n, int nitems)
     off = align_up(off + sizeof(double) * (kNStat * n + 1), 256);
     L.err = off;
     off = align_up(off + 16, 256);
+    L.steps = off;   // each grid's step count: the step keys of stochastic rounding
+    off = align_up(off + sizeof(long long) * n, 256);
     L.total = off;
     return L;
 }
@@ -115,8 +117,10 @@ struct spfm_batch {
     std::vector<GhostJob> h_ghosts;
     std::vector<StatsJob> h_stats;
     std::vector<double> h_finals;
+    std::vector<long long> h_steps;
+    int sr = 0;   // the grids round their updates stochastically (they share the mode)
     cudaGraphExec_t exec = nullptr;
-    int graph_stencil = -1, graph_kind = -1;
+    int graph_stencil = -1, graph_kind = -1, graph_sr = -1;
     std::string err;
     ~spfm_batch()
     {
@@ -161,12 +165,14 @@ static cudaError_t set_depth(spfm_batch *b, int depth)
 }
 
 // one step of every grid: persistent step kernel (one per tile shape in the
-// list), then the ghost faces of the buffers it wrote
-static cudaError_t launch_one(spfm_batch *b, int parity, int stencil, int kind)
+// list), then the ghost faces of the buffers it wrote; sub: the step's index
+// since the device step counters were last advanced
+static cudaError_t launch_one(spfm_batch *b, int parity, int stencil, int kind, int sub)
 {
     const void *grids = b->scratch + b->L.grids;
     const BatchItem *items = (const BatchItem *)(b->scratch + b->L.items);
     int *err = (int *)(b->scratch + b->L.err);
+    const long long *steps = (const long long *)(b->scratch + b->L.steps);
     cudaError_t e;
     if (b->dtype == SPFM_F64) {
         e = launch_batch_f64(grids, items, b->nitems, parity, err, stencil, kind, b->stream);
@@ -175,12 +181,13 @@ static cudaError_t launch_one(spfm_batch *b, int parity, int stencil, int kind)
         // the list (their grids differ, so the second needs nothing of the first)
         e = cudaSuccess;
         if (b->nitems0 > 0)
-            e = launch_batch_f32(grids, items, b->nitems0, parity, err, stencil, kind, b->stream, 0);
+            e = launch_batch_f32(grids, items, b->nitems0, parity, err, stencil, kind, b->stream, 0, b->sr, steps,
+                                 sub);
         if (e == cudaSuccess && b->nitems > b->nitems0)
             e = launch_batch_f32(grids, items + b->nitems0, b->nitems - b->nitems0, parity, err, stencil, kind,
-                                 b->stream, 1);
+                                 b->stream, 1, b->sr, steps, sub);
     } else {
-        e = launch_batch_bf16(grids, items, b->nitems, parity, err, stencil, kind, b->stream);
+        e = launch_batch_bf16(grids, items, b->nitems, parity, err, stencil, kind, b->stream, b->sr, steps, sub);
     }
     if (e != cudaSuccess) return e;
     return launch_fill_ghosts_batch((const GhostJob *)(b->scratch + b->L.ghosts), b->n, b->dtype,
@@ -189,7 +196,7 @@ static cudaError_t launch_one(spfm_batch *b, int parity, int stencil, int kind)
 
 static cudaError_t capture_graph(spfm_batch *b, int stencil, int kind)
 {
-    if (b->exec && b->graph_stencil == stencil && b->graph_kind == kind) return cudaSuccess;
+    if (b->exec && b->graph_stencil == stencil && b->graph_kind == kind && b->graph_sr == b->sr) return cudaSuccess;
     if (b->exec) {
         cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
@@ -198,7 +205,9 @@ static cudaError_t capture_graph(spfm_batch *b, int stencil, int kind)
     cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     cudaError_t le = cudaSuccess;
-    for (int s = 0; s < kGraphSteps && le == cudaSuccess; ++s) le = launch_one(b, s & 1, stencil, kind);
+    for (int s = 0; s < kGraphSteps && le == cudaSuccess; ++s) le = launch_one(b, s & 1, stencil, kind, s);
+    if (le == cudaSuccess && b->sr)
+        le = launch_advance_steps((long long *)(b->scratch + b->L.steps), b->n, kGraphSteps, b->stream);
     e = cudaStreamEndCapture(b->stream, &graph);
     if (le != cudaSuccess) e = le;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
@@ -206,11 +215,27 @@ static cudaError_t capture_graph(spfm_batch *b, int stencil, int kind)
     if (e == cudaSuccess) {
         b->graph_stencil = stencil;
         b->graph_kind = kind;
+        b->graph_sr = b->sr;
     } else {
         b->exec = nullptr;
     }
     return e;
 }
+
+namespace spfm {
+
+__global__ void advance_steps_kernel(long long *steps, int n, int k)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) steps[i] += k;
+}
+
+cudaError_t launch_advance_steps(long long *steps, int n, int k, cudaStream_t st)
+{
+    advance_steps_kernel<<<(n + 255) / 256, 256, 0, st>>>(steps, n, k);
+    return cudaGetLastError();
+}
+
+}  // namespace spfm
 
 extern "C" {
 
@@ -247,6 +272,7 @@ spfm_status spfm_batch_create(spfm_grid *const *grids, int n, void *scratch, siz
     b->h_ghosts.resize(n);
     b->h_stats.resize(n);
     b->h_finals.resize((size_t)kNStat * n + 1);
+    b->h_steps.resize(n);
     cudaError_t e = set_depth(b, kBatchZChunk);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->scratch + L.err, 0, 16, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -267,11 +293,15 @@ spfm_status spfm_batch_step(spfm_batch *b, int n_steps, const spfm_step_args *ar
         return bfail(b, SPFM_EINVAL, "spfm_batch_step: SPFM_TI_LOCAL is not available for batches");
     const size_t rec = grid_record_bytes(b->dtype);
     cudaError_t e = cudaSuccess;
+    b->sr = b->grids[0]->rounding == SPFM_ROUND_STOCHASTIC ? 1 : 0;
     for (int i = 0; i < b->n; ++i) {
         spfm_grid *g = b->grids[i];
         const spfm_step_args &a = args[i];
         if (a.stencil != stencil || a.scheme != scheme)
             return bfail(b, SPFM_EINVAL, "spfm_batch_step: all grids of a batch share stencil and scheme");
+        if ((g->rounding == SPFM_ROUND_STOCHASTIC ? 1 : 0) != b->sr)
+            return bfail(b, SPFM_EINVAL, "spfm_batch_step: all grids of a batch share the rounding mode");
+        b->h_steps[i] = g->steps;
         Model m;
         spfm_status st = build_model(g, a.M, a.Gamma, a.lambda, a.dx, a.dt, a.dF, a.stencil, a.scheme, m);
         if (st != SPFM_OK) {
@@ -310,6 +340,9 @@ spfm_status spfm_batch_step(spfm_batch *b, int n_steps, const spfm_step_args *ar
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->scratch + b->L.ghosts, b->h_ghosts.data(), sizeof(GhostJob) * b->n,
                             cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && b->sr)
+        e = cudaMemcpyAsync(b->scratch + b->L.steps, b->h_steps.data(), sizeof(long long) * b->n,
+                            cudaMemcpyHostToDevice, b->stream);
     if (e != cudaSuccess) return bfail(b, SPFM_ECUDA, cudaGetErrorString(e));
     int s = 0;
     // graphs need a capturable stream (not the legacy default stream)
@@ -321,8 +354,13 @@ spfm_status spfm_batch_step(spfm_batch *b, int n_steps, const spfm_step_args *ar
             if (e != cudaSuccess) return bfail(b, SPFM_ECUDA, cudaGetErrorString(e));
         }
     }
+    const int s0 = s;   // the graphs advanced the device step counters up to here
     for (; s < n_steps; ++s) {
-        e = launch_one(b, s & 1, stencil, kind);
+        e = launch_one(b, s & 1, stencil, kind, s - s0);
+        if (e != cudaSuccess) return bfail(b, SPFM_ECUDA, cudaGetErrorString(e));
+    }
+    if (b->sr && n_steps > s0) {
+        e = launch_advance_steps((long long *)(b->scratch + b->L.steps), b->n, n_steps - s0, b->stream);
         if (e != cudaSuccess) return bfail(b, SPFM_ECUDA, cudaGetErrorString(e));
     }
     for (int i = 0; i < b->n; ++i) {

@@ -20,6 +20,10 @@ struct spfm_grid {
     // model of the last step (stats: energy, estimator)
     double M = 1.0, Gamma = 1.0, lambda = 0.0, dx = 1.0, dF = 0.0;
     int stencil = 26, scheme = SPFM_TI_GLOBAL;
+    // rounding of the update (spfm_set_rounding) and the mixed seed of SPFM_ROUND_STOCHASTIC
+    int rounding = SPFM_ROUND_NEAREST;
+    uint32_t sr_seed = 0;
+    bool skip_copy = false;   // spfm_debug_skip_copy: the next step launch skips one copy
     std::string err;
 };
 
@@ -88,6 +92,7 @@ void fill_coef(const spfm_grid *g, const Model &m, double dt, int stencil, spfm:
     c.nkmudt = (T)(-m.kmu * dt);
     c.nkapdt = (T)(-m.kappa * dt);
     c.interp = m.interp;
+    c.sr_seed = g->sr_seed;
 }
 
 // TI_n constants of the step kernels: lambda/2, 1/(2 dx), 2 dx/lambda and the

@@ -80,7 +80,34 @@ struct StepCoef {
     T half_lam, inv_2dx, two_dx_over_lam, eps;
     // CF models: interpolation function of the driving term, 0 h3, 1 h5, 2 h_Abel
     int interp;
+    // stochastic rounding of the update (SPFM_ROUND_STOCHASTIC): the grid's mixed
+    // seed, and the key of the step a single-grid launch computes (sr_step_key)
+    uint32_t sr_seed, sr_key;
 };
+
+// Counter-based random bits of the stochastic rounding: the 32-bit integer
+// hash "lowbias32" of C. Wellons ("Prospecting for hash functions", 2018),
+// applied to (padded cell index) xor (step key); the step key mixes the grid's
+// seed with its own step count, so a grid draws the same bits alone and in any
+// batch.
+__host__ __device__ inline uint32_t sr_hash(uint32_t x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+__host__ __device__ inline uint32_t sr_seed_mix(unsigned long long seed)
+{
+    return sr_hash((uint32_t)seed ^ sr_hash((uint32_t)(seed >> 32) + 0x9e3779b9u));
+}
+__host__ __device__ inline uint32_t sr_step_key(uint32_t seed_mix, long long step)
+{
+    const unsigned long long s = (unsigned long long)step;
+    return sr_hash(seed_mix ^ sr_hash((uint32_t)s ^ sr_hash((uint32_t)(s >> 32))));
+}
 
 // the CF models of Tab. 2 (any interpolation function)
 __host__ __device__ inline bool is_fd_scheme(int scheme)
@@ -136,6 +163,7 @@ struct LaunchCfg {
     int stencil;   // 6, 18, 26
     int scheme;    // SPFM_TI_GLOBAL, SPFM_TI_LOCAL, SPFM_FD
     int mode;      // kWaitFaces | kWaitAll | kImages
+    int rounding = SPFM_ROUND_NEAREST;   // SPFM_ROUND_STOCHASTIC: the *_sr kernels
 };
 
 // How a step launch sits in the stream (programmatic dependent launch):
@@ -143,7 +171,9 @@ struct LaunchCfg {
 //   kWaitAll    every box waits for the previous kernel
 //   kImages     all faces periodic: the step writes the ghost images of its new cells
 //               itself (no face kernel follows) and lets the next step launch early
-constexpr int kWaitFaces = 1, kWaitAll = 2, kImages = 4;
+//   kSkipCopy   test of the bounded waits: the first CTA skips one plane's copy
+//               (spfm_debug_skip_copy), its waits give up and set the error word
+constexpr int kWaitFaces = 1, kWaitAll = 2, kImages = 4, kSkipCopy = 8;
 
 // TMA tensor maps of a grid's two field buffers, encoded on first use (tma.cu).
 struct TmaCache {
@@ -180,6 +210,16 @@ cudaError_t launch_step_f64_img(const StepCoef<double> &c, const double *src, do
 cudaError_t launch_step_bf16_img(const StepCoef<float> &c, const __nv_bfloat16 *src,
                                  __nv_bfloat16 *dst, int *err, LaunchCfg cfg, TmaCache *tma, int which,
                                  cudaStream_t st);
+// the same with stochastic rounding of the update (step_*_sr.cu; cfg.rounding
+// set; the dispatch above forwards to them)
+cudaError_t launch_step_f32_sr(const StepCoef<float> &c, const float *src, float *dst, int *err, LaunchCfg cfg,
+                               TmaCache *tma, int which, cudaStream_t st);
+cudaError_t launch_step_f32_img_sr(const StepCoef<float> &c, const float *src, float *dst, int *err,
+                                   LaunchCfg cfg, TmaCache *tma, int which, cudaStream_t st);
+cudaError_t launch_step_bf16_sr(const StepCoef<float> &c, const __nv_bfloat16 *src, __nv_bfloat16 *dst,
+                                int *err, LaunchCfg cfg, TmaCache *tma, int which, cudaStream_t st);
+cudaError_t launch_step_bf16_img_sr(const StepCoef<float> &c, const __nv_bfloat16 *src, __nv_bfloat16 *dst,
+                                    int *err, LaunchCfg cfg, TmaCache *tma, int which, cudaStream_t st);
 
 // Initial ideal profiles and FP64 diagnostics (stats.cu).
 struct InitArgs {
@@ -249,12 +289,22 @@ int batch_items_bf16(const GridGeom &g, int grid_index, int zchunk, BatchItem *o
 void batch_fill_grid_f32(void *slot, const StepCoef<float> &c, void *const field[2], int cur, TmaCache *tma);
 void batch_fill_grid_f64(void *slot, const StepCoef<double> &c, void *const field[2], int cur, TmaCache *tma);
 void batch_fill_grid_bf16(void *slot, const StepCoef<float> &c, void *const field[2], int cur, TmaCache *tma);
+// sr: stochastic rounding (the *_sr kernels), whose step keys come from
+// steps[grid] (device: each grid's step count at the start of the call) + sub
+// (the launch's position in the call)
 cudaError_t launch_batch_f32(const void *grids, const BatchItem *work, int nwork, int parity, int *err,
-                             int stencil, int kind, cudaStream_t st, int shape);
+                             int stencil, int kind, cudaStream_t st, int shape, int sr, const long long *steps,
+                             int sub);
 cudaError_t launch_batch_f64(const void *grids, const BatchItem *work, int nwork, int parity, int *err,
                              int stencil, int kind, cudaStream_t st);
 cudaError_t launch_batch_bf16(const void *grids, const BatchItem *work, int nwork, int parity, int *err,
-                              int stencil, int kind, cudaStream_t st);
+                              int stencil, int kind, cudaStream_t st, int sr, const long long *steps, int sub);
+cudaError_t launch_batch_f32_sr(const void *grids, const BatchItem *work, int nwork, int parity, int *err,
+                                int stencil, int kind, cudaStream_t st, int shape, const long long *steps, int sub);
+cudaError_t launch_batch_bf16_sr(const void *grids, const BatchItem *work, int nwork, int parity, int *err,
+                                 int stencil, int kind, cudaStream_t st, const long long *steps, int sub);
+// steps[i] += k for the n grids of a batch (after the k steps of a call or graph)
+cudaError_t launch_advance_steps(long long *steps, int n, int k, cudaStream_t st);
 
 // Ghost refresh of every grid of a batch: job i fills buffer cur ^ parity of grid i.
 struct GhostJob {

@@ -1,27 +1,29 @@
 // BF16 storage with FP32 compute: instantiations of the step kernel.
 #include "step_kernel.cuh"
+#include "tiles.h"
 
 namespace spfm {
 cudaError_t launch_step_bf16(const StepCoef<float> &c, const __nv_bfloat16 *src, __nv_bfloat16 *dst, int *err,
                             LaunchCfg cfg, TmaCache *tma, int which, cudaStream_t st)
 {
     if (cfg.mode & kImages) return launch_step_bf16_img(c, src, dst, err, cfg, tma, which, st);
-    using Sh = TileShape<__nv_bfloat16, float, 8, 16>;
+    if (cfg.rounding == SPFM_ROUND_STOCHASTIC) return launch_step_bf16_sr(c, src, dst, err, cfg, tma, which, st);
+    using Sh = TileShape<__nv_bfloat16, float, kBfTX, kBfTY>;
     const CUtensorMap *map = cached_map(tma, which, c.g, SPFM_BF16, src, Sh::SW, Sh::ROWS);
-    return launch_step_t<__nv_bfloat16, float, 8, 16, false>(c, src, dst, err, cfg, map, st);
+    return launch_step_t<__nv_bfloat16, float, kBfTX, kBfTY, false>(c, src, dst, err, cfg, map, st);
 }
 
 size_t batch_grid_bytes_bf16() { return sizeof(BatchGrid<float>); }
 
 int batch_items_bf16(const GridGeom &g, int grid_index, int zchunk, BatchItem *out, int)
 {
-    return batch_items_t<__nv_bfloat16, float, 8, 16>(g, grid_index, zchunk, out, 0);
+    return batch_items_t<__nv_bfloat16, float, kBfTX, kBfTY>(g, grid_index, zchunk, out, 0);
 }
 
 void batch_fill_grid_bf16(void *slot, const StepCoef<float> &c, void *const field[2], int cur,
                           TmaCache *tma)
 {
-    using Sh = TileShape<__nv_bfloat16, float, 8, 16>;
+    using Sh = TileShape<__nv_bfloat16, float, kBfTX, kBfTY>;
     BatchGrid<float> *b = (BatchGrid<float> *)slot;
     b->C = c;
     b->PC = make_pack_coef<float>(c);
@@ -39,8 +41,10 @@ void batch_fill_grid_bf16(void *slot, const StepCoef<float> &c, void *const fiel
 }
 
 cudaError_t launch_batch_bf16(const void *grids, const BatchItem *work, int nwork, int parity,
-                              int *err, int stencil, int kind, cudaStream_t st)
+                              int *err, int stencil, int kind, cudaStream_t st, int sr, const long long *steps,
+                              int sub)
 {
-    return launch_batch_t<__nv_bfloat16, float, 8, 16>(grids, work, nwork, parity, err, stencil, kind, st);
+    if (sr) return launch_batch_bf16_sr(grids, work, nwork, parity, err, stencil, kind, st, steps, sub);
+    return launch_batch_t<__nv_bfloat16, float, kBfTX, kBfTY>(grids, work, nwork, parity, err, stencil, kind, st);
 }
 }  // namespace spfm

@@ -1,23 +1,13 @@
 // FP32 storage, FP32 (packed f32x2) compute: instantiations of the step kernel.
 #include "step_kernel.cuh"
-
-// tile of the FP32 kernel: SPFM_F32_TX threads of 4 cells in x, SPFM_F32_TY rows
-#ifndef SPFM_F32_TX
-#define SPFM_F32_TX 16
-#endif
-#ifndef SPFM_F32_TY
-#define SPFM_F32_TY 16
-#endif
-// the square tile of FP32 batch items of shape 1: 8 threads of 4 cells, 32 rows
-// (32 x 32 cells, the same 128 consumer threads), for grids narrower than the
-// 64-cell tile or whose x extent it would pad
-constexpr int kSqTX = 8, kSqTY = 32;
+#include "tiles.h"
 
 namespace spfm {
 cudaError_t launch_step_f32(const StepCoef<float> &c, const float *src, float *dst, int *err,
                             LaunchCfg cfg, TmaCache *tma, int which, cudaStream_t st)
 {
     if (cfg.mode & kImages) return launch_step_f32_img(c, src, dst, err, cfg, tma, which, st);
+    if (cfg.rounding == SPFM_ROUND_STOCHASTIC) return launch_step_f32_sr(c, src, dst, err, cfg, tma, which, st);
     using Sh = TileShape<float, float, SPFM_F32_TX, SPFM_F32_TY>;
     const CUtensorMap *map = cached_map(tma, which, c.g, SPFM_F32, src, Sh::SW, Sh::ROWS);
     return launch_step_t<float, float, SPFM_F32_TX, SPFM_F32_TY, false>(c, src, dst, err, cfg, map, st);
@@ -59,8 +49,10 @@ void batch_fill_grid_f32(void *slot, const StepCoef<float> &c, void *const field
 }
 
 cudaError_t launch_batch_f32(const void *grids, const BatchItem *work, int nwork, int parity,
-                              int *err, int stencil, int kind, cudaStream_t st, int shape)
+                              int *err, int stencil, int kind, cudaStream_t st, int shape, int sr,
+                              const long long *steps, int sub)
 {
+    if (sr) return launch_batch_f32_sr(grids, work, nwork, parity, err, stencil, kind, st, shape, steps, sub);
     if (shape == 1)
         return launch_batch_t<float, float, kSqTX, kSqTY, true>(grids, work, nwork, parity, err, stencil, kind, st);
     return launch_batch_t<float, float, SPFM_F32_TX, SPFM_F32_TY>(grids, work, nwork, parity, err, stencil, kind, st);

@@ -1,18 +1,13 @@
 // FP32 storage, FP32 (packed f32x2) compute, all faces periodic: the step
 // kernels that also write the periodic ghost images of their new cells.
 #include "step_kernel.cuh"
-
-#ifndef SPFM_F32_TX
-#define SPFM_F32_TX 16
-#endif
-#ifndef SPFM_F32_TY
-#define SPFM_F32_TY 16
-#endif
+#include "tiles.h"
 
 namespace spfm {
 cudaError_t launch_step_f32_img(const StepCoef<float> &c, const float *src, float *dst, int *err,
                                 LaunchCfg cfg, TmaCache *tma, int which, cudaStream_t st)
 {
+    if (cfg.rounding == SPFM_ROUND_STOCHASTIC) return launch_step_f32_img_sr(c, src, dst, err, cfg, tma, which, st);
     using Sh = TileShape<float, float, SPFM_F32_TX, SPFM_F32_TY>;
     const CUtensorMap *map = cached_map(tma, which, c.g, SPFM_F32, src, Sh::SW, Sh::ROWS);
     return launch_step_t<float, float, SPFM_F32_TX, SPFM_F32_TY, true>(c, src, dst, err, cfg, map, st);

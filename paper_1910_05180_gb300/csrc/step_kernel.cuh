@@ -353,6 +353,52 @@ template <> struct TanhPk<double> {
     static __device__ __forceinline__ D2 eval(D2 x, bool) { return {tanh(x.x), tanh(x.y)}; }
 };
 
+// ---------------------------------------------------- stochastic rounding
+
+// Stochastic rounding of the update phi + inc to the storage type S (FP32 or
+// BF16): with a the largest value of S not above the exact sum and g the
+// spacing of S above a, the stored value is a + g with probability
+// (phi + inc - a) / g and a otherwise, so that its expectation is the exact
+// update; an exactly representable sum (inc = 0 in particular) is stored as
+// is.  It is computed as round-down(phi + (inc + u g)) with u uniform in
+// [0, 1) on a 2^-16 grid (16 bits of h per cell): since inc + u g spans
+// exactly one spacing above a, the round-down lands on a or a + g.  The
+// rounding of inc + u g in FP32 (2^-24 of g) is far below the step.
+template <class S> struct MantBits;
+template <> struct MantBits<float> { static constexpr int v = 23; };
+template <> struct MantBits<__nv_bfloat16> { static constexpr int v = 7; };
+
+// spacing of S above a >= 0 (from a's exponent; 0 for |a| < 2^(bits - 126))
+__device__ __forceinline__ float spacing_above(float a, int bits)
+{
+    const int e = (int)(__float_as_uint(a) & 0x7f800000u) - (bits << 23);
+    return __int_as_float(e > 0 ? e : 0);
+}
+
+// the largest BF16 value not above v (v an FP32 value)
+__device__ __forceinline__ float bf16_round_down(float v)
+{
+    uint32_t b = __float_as_uint(v);
+    if ((b & 0x80000000u) && (b & 0xffffu)) b = (b & 0xffff0000u) + 0x10000u;   // away from zero
+    else b &= 0xffff0000u;
+    return __uint_as_float(b);
+}
+
+template <class S>
+__device__ __forceinline__ float2 sr_update(float2 ph, float2 inc, uint32_t h)
+{
+    constexpr int mb = MantBits<S>::v;
+    float2 a = __fadd2_rd(ph, inc);
+    if constexpr (mb == 7) { a.x = bf16_round_down(a.x); a.y = bf16_round_down(a.y); }
+    const float2 g = make_float2(spacing_above(fabsf(a.x), mb), spacing_above(fabsf(a.y), mb));
+    const float2 u = __fadd2_rn(make_float2(__uint_as_float(0x3f800000u | ((h << 7) & 0x007fff80u)),
+                                            __uint_as_float(0x3f800000u | ((h >> 9) & 0x007fff80u))),
+                                make_float2(-1.0f, -1.0f));
+    float2 x = __fadd2_rd(ph, __ffma2_rn(u, g, inc));
+    if constexpr (mb == 7) { x.x = bf16_round_down(x.x); x.y = bf16_round_down(x.y); }
+    return x;
+}
+
 // TI_n factor w = -dt (potential / q + 4 M dF / (lambda Gamma)) of a pack of
 // cells with s = 1 - 2 phi, u = s^2 and the profile-inversion gradient g
 // (Sec. 2.1, TI_n): n = g / |g|, t_i = tanh(2 dx n_i / lambda), the 13
@@ -475,14 +521,17 @@ __device__ __forceinline__ void store_z_images(const GridGeom &g, S *dst, int x,
 // tiles a CTA processes: plane i of this tile is ring slot base + i.  The
 // producer waits for its copies in flight before returning when drain is set.
 // Returns false when a bounded wait gave up (the error word is set).
-template <class S, class T, int STENCIL, int KIND, int TX, int TY, int RPT_, bool IMG = false>
+// SR: stochastic rounding of the update (FP32 compute only), random bits from
+// sr_hash(padded cell index xor sr_key).
+template <class S, class T, int STENCIL, int KIND, int TX, int TY, int RPT_, bool IMG = false, bool SR = false>
 __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T> &PC,
                                           const S *__restrict__ src, S *__restrict__ dst,
                                           int *__restrict__ err, const CUtensorMap *tmap, int bx,
                                           int by, int zc0, int zc1, S *__restrict__ stages,
                                           uint64_t *full, uint64_t *empty, int base, bool drain,
-                                          int mode = 0)
+                                          int mode = 0, uint32_t sr_key = 0)
 {
+    static_assert(!SR || sizeof(T) == 4, "stochastic rounding is for FP32 compute");
     using Sh = TileShape<S, T, TX, TY, RPT_>;
     using K = Pk<T>;
     using P = typename K::P;
@@ -509,11 +558,18 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
             ((mode & kWaitFaces) &&
              (bx == 0 || x0 + W >= g.nx || by == 0 || y0 + TY >= g.ny || zc0 == 0 || zc1 == g.nz)))
             asm volatile("griddepcontrol.wait;" ::: "memory");
+        // kSkipCopy (a test of the bounded waits): the first CTA never fills the
+        // stage of its plane 1, so its consumers' wait for that stage gives up
+        const bool skip = (mode & kSkipCopy) && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0;
         int issued = 0;
         bool ok = true;
         for (int i = 0; i < nplanes; ++i) {
             const int I = base + i, s = I % NS;
             if (I >= NS && !mbar_wait_sleep(&empty[s], ((I / NS) - 1) & 1)) { ok = false; break; }
+            if (skip && i == 1) {
+                ++issued;
+                continue;
+            }
             if (tmap) {
                 mbar_expect_tx(&full[s], (uint32_t)Sh::BOX_BYTES);
                 // one box: padded x from the 16-byte chunk left of the tile (x0 + off
@@ -534,10 +590,11 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
             ++issued;
         }
         if (!ok) atomicOr(err, 1);
-        // never leave with copies in flight
+        // never leave with copies in flight: wait for each stage's copy (a stage
+        // whose wait gives up does not stop the waits for the others)
         if (drain || !ok)
             for (int I = max(0, base + issued - NS); I < base + issued; ++I)
-                if (!mbar_wait_sleep(&full[I % NS], (I / NS) & 1)) { atomicOr(err, 2); break; }
+                if (!mbar_wait_sleep(&full[I % NS], (I / NS) & 1)) atomicOr(err, 2);
         return ok;
     }
 
@@ -652,6 +709,9 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
             for (int r = 0; r < RPT; ++r) {
                 if (gy + r >= g.ny || gx >= g.nx) continue;
                 T outv[VX];
+                // padded index of the row's first cell (32-bit, wraps): the cell's
+                // part of the stochastic-rounding hash
+                const uint32_t sr_row = SR ? (uint32_t)cell_index(g, gx, gy + r, oz) : 0u;
                 if constexpr (KIND == 5) {
                     // up to 13 groups counted at run time (in a batch the coefficients
                     // sit in global memory): the running fraction over every pack of
@@ -662,7 +722,9 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
                     for (int q = 0; q < NP; ++q) {
                         const P ph = z[r].c[q];
                         const P t = K::add(K::sub(m[r].c[q], ph), K::sub(p[r].c[q], ph));
-                        acc[q] = K::add(K::fma(PC.ct, t, ph), z[r].h[q]);
+                        // SR: the increment alone, phi is added once in sr_update
+                        if constexpr (SR) acc[q] = K::fma(PC.ct, t, z[r].h[q]);
+                        else acc[q] = K::add(K::fma(PC.ct, t, ph), z[r].h[q]);
                         if (STENCIL != 6) acc[q] = K::add(acc[q], K::add(m[r].g[q], p[r].g[q]));
                         sg[q] = K::fma(PC.m2, ph, PC.one);
                         q1[q] = K::mul(ph, K::sub(PC.one, ph));
@@ -684,7 +746,8 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
                     }
 #pragma unroll
                     for (int q = 0; q < NP; ++q) {
-                        const P o = K::fma(q1[q], K::fma(sg[q], K::div(num[q], den[q]), PC.nkmu), acc[q]);
+                        P o = K::fma(q1[q], K::fma(sg[q], K::div(num[q], den[q]), PC.nkmu), acc[q]);
+                        if constexpr (SR) o = sr_update<S>(z[r].c[q], o, sr_hash((sr_row + 2 * q) ^ sr_key));
                         outv[2 * q] = o.x;
                         outv[2 * q + 1] = o.y;
                     }
@@ -693,7 +756,10 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
                     for (int q = 0; q < NP; ++q) {
                         const P ph = z[r].c[q];
                         const P t = K::add(K::sub(m[r].c[q], ph), K::sub(p[r].c[q], ph));
-                        P acc = K::add(K::fma(PC.ct, t, ph), z[r].h[q]);      // phi + dt * Laplacian
+                        // phi + dt * Laplacian (SR: the increment alone, phi is added in sr_update)
+                        P acc;
+                        if constexpr (SR) acc = K::fma(PC.ct, t, z[r].h[q]);
+                        else acc = K::add(K::fma(PC.ct, t, ph), z[r].h[q]);
                         if (STENCIL != 6) acc = K::add(acc, K::add(m[r].g[q], p[r].g[q]));
                         const P sg = K::fma(PC.m2, ph, PC.one);               // s = 1 - 2 phi
                         const P q1 = K::mul(ph, K::sub(PC.one, ph));          // q = phi (1 - phi)
@@ -727,7 +793,8 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
                             }
                             w = K::fma(sg, K::div(num, den), PC.nkmu);
                         }
-                        const P o = K::fma(q1, w, acc);
+                        P o = K::fma(q1, w, acc);
+                        if constexpr (SR) o = sr_update<S>(ph, o, sr_hash((sr_row + 2 * q) ^ sr_key));
                         outv[2 * q] = o.x;
                         outv[2 * q + 1] = o.y;
                     }
@@ -786,8 +853,11 @@ template <class S> struct MinBlocks { static constexpr int value = SPFM_MIN_CTAS
 template <> struct MinBlocks<float> { static constexpr int value = 4; };
 template <class S> struct BatchMinBlocks { static constexpr int value = SPFM_MIN_CTAS; };
 
-template <class S, class T, int STENCIL, int KIND, int TX, int TY, int RPT_, bool IMG>
-__global__ void __launch_bounds__(TileShape<S, T, TX, TY, RPT_>::NTHREADS, RPT_ == 1 ? 2 : MinBlocks<S>::value)
+// (the stochastic-rounding kernels keep three CTAs per SM: at four their extra
+// registers spill)
+template <class S, class T, int STENCIL, int KIND, int TX, int TY, int RPT_, bool IMG, bool SR = false>
+__global__ void __launch_bounds__(TileShape<S, T, TX, TY, RPT_>::NTHREADS,
+                                  RPT_ == 1 ? 2 : (SR ? SPFM_MIN_CTAS : MinBlocks<S>::value))
     spfm_step_kernel(const StepCoef<T> C, const PackCoef<T> PC, const S *__restrict__ src,
                      S *__restrict__ dst, int *__restrict__ err, int zchunk,
                      const __grid_constant__ CUtensorMap tmap, int use_tmap, int mode)
@@ -808,9 +878,9 @@ __global__ void __launch_bounds__(TileShape<S, T, TX, TY, RPT_>::NTHREADS, RPT_ 
     __syncthreads();
     const int zc0 = blockIdx.z * zchunk;
     const int zc1 = min(zc0 + zchunk, C.g.nz);
-    step_tile<S, T, STENCIL, KIND, TX, TY, RPT_, IMG>(C, PC, src, dst, err, use_tmap ? &tmap : nullptr,
-                                                 blockIdx.x, blockIdx.y, zc0, zc1, stages, full, empty, 0,
-                                                 true, mode);
+    step_tile<S, T, STENCIL, KIND, TX, TY, RPT_, IMG, SR>(C, PC, src, dst, err, use_tmap ? &tmap : nullptr,
+                                                     blockIdx.x, blockIdx.y, zc0, zc1, stages, full, empty, 0,
+                                                     true, mode, C.sr_key);
 }
 
 // ------------------------------------------------------------------- batches
@@ -831,10 +901,13 @@ struct BatchGrid {
 // Persistent kernel over a packed work-list of items of one tile shape (TX,
 // TY): CTA b takes items b, b + gridDim.x, ...  Step `parity` reads buffer
 // cur ^ parity.  SQ: the items use the square tile's TMA maps (map_sq).
-template <class S, class T, int STENCIL, int KIND, int TX, int TY, bool SQ>
+// SR: stochastic rounding, the step key of grid i from sr_step_key(its seed,
+// steps[i] + sub).
+template <class S, class T, int STENCIL, int KIND, int TX, int TY, bool SQ, bool SR = false>
 __global__ void __launch_bounds__(TileShape<S, T, TX, TY>::NTHREADS, BatchMinBlocks<S>::value)
     spfm_batch_kernel(const BatchGrid<T> *__restrict__ grids, const BatchItem *__restrict__ work,
-                      int nwork, int parity, int *__restrict__ err)
+                      int nwork, int parity, int *__restrict__ err, const long long *__restrict__ steps,
+                      int sub)
 {
     using Sh = TileShape<S, T, TX, TY>;
     __shared__ __align__(128) S stages[Sh::NS * Sh::STAGE];
@@ -856,9 +929,10 @@ __global__ void __launch_bounds__(TileShape<S, T, TX, TY>::NTHREADS, BatchMinBlo
         if (map && threadIdx.x == Sh::NCONS)
             asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
         const bool last = w + (int)gridDim.x >= nwork;
-        if (!step_tile<S, T, STENCIL, KIND, TX, TY, SPFM_ROWS_PER_THREAD>(bg.C, bg.PC, (const S *)bg.field[cur],
-                                                    (S *)bg.field[cur ^ 1], err, map, it.bx, it.by,
-                                                    it.zc0, it.zc1, stages, full, empty, base, last))
+        const uint32_t key = SR ? sr_step_key(bg.C.sr_seed, steps[it.grid] + sub) : 0u;
+        if (!step_tile<S, T, STENCIL, KIND, TX, TY, SPFM_ROWS_PER_THREAD, false, SR>(
+                bg.C, bg.PC, (const S *)bg.field[cur], (S *)bg.field[cur ^ 1], err, map, it.bx, it.by, it.zc0,
+                it.zc1, stages, full, empty, base, last, 0, key))
             return;
         base += it.zc1 - it.zc0 + 2;
     }
@@ -881,9 +955,10 @@ inline int batch_items_t(const GridGeom &g, int grid_index, int zchunk, BatchIte
     return n;
 }
 
-template <class S, class T, int TX, int TY, bool SQ = false>
+template <class S, class T, int TX, int TY, bool SQ = false, bool SR = false>
 cudaError_t launch_batch_t(const void *grids, const BatchItem *work, int nwork, int parity, int *err,
-                           int stencil, int kind, cudaStream_t st)
+                           int stencil, int kind, cudaStream_t st, const long long *steps = nullptr,
+                           int sub = 0)
 {
     using Sh = TileShape<S, T, TX, TY>;
     int dev = 0, sms = 152;
@@ -893,8 +968,9 @@ cudaError_t launch_batch_t(const void *grids, const BatchItem *work, int nwork, 
     if (ctas > nwork) ctas = nwork;
     if (ctas < 1) return cudaSuccess;
     const BatchGrid<T> *bg = (const BatchGrid<T> *)grids;
-#define SPFM_BLAUNCH(ST, KD) \
-    spfm_batch_kernel<S, T, ST, KD, TX, TY, SQ><<<ctas, Sh::NTHREADS, 0, st>>>(bg, work, nwork, parity, err)
+#define SPFM_BLAUNCH(ST, KD)                                                                               \
+    spfm_batch_kernel<S, T, ST, KD, TX, TY, SQ, SR><<<ctas, Sh::NTHREADS, 0, st>>>(bg, work, nwork, parity, err, \
+                                                                                 steps, sub)
 #define SPFM_BBY_KIND(ST)                      \
     do {                                       \
         if (kind == 0) SPFM_BLAUNCH(ST, 0);    \
@@ -920,7 +996,7 @@ inline int pick_zchunk(int tiles_xy, int nz, int target)
 }
 
 // IMG: the kernels that write the periodic ghost images (cfg.mode has kImages)
-template <class S, class T, int TX, int TY, bool IMG>
+template <class S, class T, int TX, int TY, bool IMG, bool SR = false>
 cudaError_t launch_step_t(const StepCoef<T> &c, const S *src, S *dst, int *err, LaunchCfg cfg,
                           const CUtensorMap *tmap, cudaStream_t st)
 {
@@ -962,7 +1038,7 @@ cudaError_t launch_step_t(const StepCoef<T> &c, const S *src, S *dst, int *err, 
         return cudaLaunchKernelEx(&lc, kern, c, pc, src, dst, err, zchunk, map, use, mode);
     };
     cudaError_t le = cudaSuccess;
-#define SPFM_LAUNCH(ST, KD) le = go(spfm_step_kernel<S, T, ST, KD, TX, TY, R, IMG>, Sh::NTHREADS)
+#define SPFM_LAUNCH(ST, KD) le = go(spfm_step_kernel<S, T, ST, KD, TX, TY, R, IMG, SR>, Sh::NTHREADS)
 #define SPFM_BY_KIND(ST)                        \
     do {                                        \
         if (kind == 0) SPFM_LAUNCH(ST, 0);      \
@@ -971,7 +1047,7 @@ cudaError_t launch_step_t(const StepCoef<T> &c, const S *src, S *dst, int *err, 
         else if (kind == 3) SPFM_LAUNCH(ST, 3); \
         else if (kind == 4) SPFM_LAUNCH(ST, 4); \
         else if (kind == 5) SPFM_LAUNCH(ST, 5); \
-        else le = go(spfm_step_kernel<S, T, ST, 6, TX, TY, 1, IMG>, NT1); \
+        else le = go(spfm_step_kernel<S, T, ST, 6, TX, TY, 1, IMG, SR>, NT1); \
     } while (0)
     if (cfg.stencil == 6) SPFM_BY_KIND(6);
     else if (cfg.stencil == 18) SPFM_BY_KIND(18);

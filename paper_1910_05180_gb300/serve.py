@@ -22,6 +22,7 @@ from __future__ import annotations
 
 import math
 import time
+import zlib
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -84,16 +85,27 @@ def job_from_workload(w: dict) -> Job:
                stencil=w.get("stencil", 26))
 
 
-class GpuBackend:
-    """Grids and batches of the CUDA library (FP32 storage by default)."""
+def job_seed(job: Job) -> int:
+    """Seed of a job's stochastic rounding: a hash of its name, so that its
+    random bits (and its result) do not depend on the other jobs."""
+    return zlib.crc32(job.name.encode())
 
-    def __init__(self, dtype=None, stream=None):
+
+class GpuBackend:
+    """Grids and batches of the CUDA library: FP32 storage with stochastic
+    rounding of the update by default (round to nearest drops the sub-ulp
+    increments of slow interfaces near phi = 1 and biases their velocity)."""
+
+    def __init__(self, dtype=None, stream=None, rounding=None):
         import torch
 
         from . import spfm as S
         self.S = S
         self.torch = torch
         self.dtype = S.SPFM_F32 if dtype is None else dtype
+        self.rounding = S.SPFM_ROUND_STOCHASTIC if rounding is None else rounding
+        if self.dtype == S.SPFM_F64:
+            self.rounding = S.SPFM_ROUND_NEAREST
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self._batch = None
         self._members = ()
@@ -109,6 +121,7 @@ class GpuBackend:
         with self.torch.cuda.stream(self.stream):
             g = S.Grid(job.nx, job.ny, job.nz, dtype=self.dtype, bc=(S.SPFM_CONTACT,) * 6, n=job.n,
                        stream=self.stream)
+            g.set_rounding(self.rounding, job_seed(job))
             g.init_planar(job.c, job.lam, job.dx)
         return g
 
@@ -133,6 +146,24 @@ class GpuBackend:
 
     def positions(self, entries):
         return [s["position"] for s in self._batch.stats()]
+
+
+class PlainGpuBackend(GpuBackend):
+    """The one-launch-per-job path, for comparison: the same grids, rounding
+    and windows, but each job is stepped by its own spfm_step launches and
+    measured by its own stats call (no batch, no graph)."""
+
+    def release(self, handle):
+        handle.close()
+
+    def step(self, entries, n_steps: int):
+        for a in entries:
+            j = a.job
+            a.handle.step(n_steps, M=j.M, Gamma=j.Gamma, lam=j.lam, dx=j.dx, dt=j.dt, dF=j.dF,
+                          stencil=j.stencil)
+
+    def positions(self, entries):
+        return [a.handle.stats()["position"] for a in entries]
 
 
 class Server:

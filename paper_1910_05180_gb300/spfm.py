@@ -29,6 +29,7 @@ SPFM_TI_GLOBAL, SPFM_TI_LOCAL, SPFM_FD = 0, 1, 2
 SPFM_FD_H5, SPFM_FD_HABEL = 3, 4   # CF with the interpolation functions h5 and h_Abel (Tab. 2)
 SPFM_STATS_ENERGY = 1
 SPFM_TILES_WIDE, SPFM_TILES_SQUARE, SPFM_TILES_FIT = 0, 1, 2   # batch tile policies
+SPFM_ROUND_NEAREST, SPFM_ROUND_STOCHASTIC = 0, 1                 # rounding of the update
 
 TORCH_DTYPE = {SPFM_F64: torch.float64, SPFM_F32: torch.float32, SPFM_BF16: torch.bfloat16}
 STATUS_NAME = {0: "SPFM_OK", -1: "SPFM_EINVAL", -2: "SPFM_EUNSTABLE", -3: "SPFM_EPHASE",
@@ -92,6 +93,8 @@ SIGNATURES = [
     ("spfm_init_cube", _I, [_P, ctypes.POINTER(_D), _D, _D, _D]),
     ("spfm_step", _I, [_P, _I, _D, _D, _D, _D, _D, _D, _I, _I]),
     ("spfm_step_conserving", _I, [_P, _I, _D, _D, _D, _D, _D, _I, _I, ctypes.POINTER(_D)]),
+    ("spfm_set_rounding", _I, [_P, _I, ctypes.c_ulonglong]),
+    ("spfm_debug_skip_copy", _I, [_P]),
     ("spfm_shift_x", _I, [_P, _I]),
     ("spfm_max_dt", _I, [_P, _D, _D, _D, _D, _D, _I, _I, ctypes.POINTER(_D)]),
     ("spfm_interface_stats", _I, [_P, _I, ctypes.POINTER(Stats)]),
@@ -160,6 +163,14 @@ def spfm_destroy_grid(h):
 
 def spfm_set_stream(h, stream):
     _check(load().spfm_set_stream(h, stream), h)
+
+
+def spfm_set_rounding(h, mode, seed=0):
+    _check(load().spfm_set_rounding(h, int(mode), int(seed) & 0xFFFFFFFFFFFFFFFF), h)
+
+
+def spfm_debug_skip_copy(h):
+    _check(load().spfm_debug_skip_copy(h), h)
 
 
 def spfm_init_planar(h, c, lam, dx):
@@ -300,6 +311,10 @@ class Grid:
     def step(self, n_steps, M=1.0, Gamma=1.0, lam=4.0, dx=1.0, dt=0.1, dF=0.0, stencil=26,
              scheme=SPFM_TI_GLOBAL):
         spfm_step(self.handle, n_steps, M, Gamma, lam, dx, dt, dF, stencil, scheme)
+
+    def set_rounding(self, mode, seed=0):
+        """SPFM_ROUND_NEAREST or SPFM_ROUND_STOCHASTIC (FP32/BF16) for the following steps."""
+        spfm_set_rounding(self.handle, mode, seed)
 
     def shift_x(self, cells):
         """Moving frame: phi_i <- phi_{i+cells} (end cells repeated)."""

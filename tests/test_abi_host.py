@@ -183,6 +183,22 @@ def test_euler_bound_matches_spectral_radius(lib):
         S.spfm_destroy_grid(h)
 
 
+def test_rounding_mode_validation(lib):
+    """Stochastic rounding is for FP32 and BF16 storage; unknown modes are refused."""
+    for dtype in (S.SPFM_F32, S.SPFM_BF16):
+        h = _fake_grid(lib, dtype=dtype)
+        assert lib.spfm_set_rounding(h, S.SPFM_ROUND_STOCHASTIC, 12345) == S.SPFM_OK
+        assert lib.spfm_set_rounding(h, S.SPFM_ROUND_NEAREST, 0) == S.SPFM_OK
+        assert lib.spfm_set_rounding(h, 7, 0) == S.SPFM_EINVAL
+        lib.spfm_destroy_grid(h)
+    h = _fake_grid(lib, dtype=S.SPFM_F64)
+    assert lib.spfm_set_rounding(h, S.SPFM_ROUND_STOCHASTIC, 1) == S.SPFM_EINVAL
+    assert b"FP32 and BF16" in lib.spfm_last_error(h)
+    assert lib.spfm_set_rounding(h, S.SPFM_ROUND_NEAREST, 1) == S.SPFM_OK
+    lib.spfm_destroy_grid(h)
+    assert lib.spfm_set_rounding(None, S.SPFM_ROUND_NEAREST, 0) == S.SPFM_EINVAL
+
+
 def test_last_error_is_thread_local_without_grid(lib):
     with pytest.raises(S.SpfmError):
         S.spfm_layout(_desc(dtype=9))

@@ -81,11 +81,29 @@ def test_both_arms_report_the_same_config():
     assert bench.arm_config(bench.parse(["--impl", "reference"]), w, 1) == cfg
 
 
-def test_profiled_figures_only_for_the_captured_sources(monkeypatch):
+def test_profiled_figures_only_for_the_captured_sources(monkeypatch, tmp_path):
     """The traffic and ALU-ceiling records of profiles/traffic.json are used
     only while the stencil sources hash to the captured version."""
+    import json
     key = "spfm_step_kernel_f32_27pt_ti120_512"
-    assert bench.profiled_traffic(key) is not None
+    rec = {key: {"source_hash": bench.source_hash(), "bytes_per_launch": 1.0e9},
+           "spfm_step_kernel_f32_27pt_local": {"source_hash": bench.source_hash(),
+                                               "alu_ceiling_cell_updates_per_s": 2.0e11}}
+    path = tmp_path / "traffic.json"
+    path.write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "TRAFFIC_PATH", str(path))
+    assert bench.profiled_traffic(key) == 1.0e9
     assert bench.profiled_record("spfm_step_kernel_f32_27pt_local", "alu_ceiling_cell_updates_per_s") > 0
+    assert bench.profiled_traffic("no_such_kernel") is None
     monkeypatch.setattr(bench, "source_hash", lambda names=None: "0000000000000000")
     assert bench.profiled_traffic(key) is None
+
+
+def test_committed_profile_record_names_a_source_hash():
+    """Every record of the committed traffic file carries the hash of the
+    stencil sources it was captured on (stale records read as null)."""
+    import json
+    with open(bench.TRAFFIC_PATH) as f:
+        d = json.load(f)
+    recs = [v for v in d.values() if isinstance(v, dict) and "bytes_per_launch" in v]
+    assert recs and all(len(v.get("source_hash", "")) == 16 for v in recs)
