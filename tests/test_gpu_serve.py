@@ -75,4 +75,6 @@ def test_plain_path_gives_the_served_results():
     a = {r.name: r for r in served.results}
     for r in plain.results:
         assert r.steps == a[r.name].steps
-        assert r.velocity == a[r.name].velocity
+        # fields are bit-identical; the positions come from the batched and the
+        # single-grid stats reductions, which sum in different orders
+        assert abs(r.velocity - a[r.name].velocity) <= 1e-12 * abs(a[r.name].velocity)
