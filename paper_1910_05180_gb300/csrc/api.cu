@@ -171,14 +171,14 @@ cudaStream_t stream_of(const spfm_grid *g) { return (cudaStream_t)g->d.stream; }
 
 // Refill the ghost layer of the current buffer for the given lambda and dx
 // (contact faces depend on both), and clear the device error word.
-int refresh_ghosts(spfm_grid *g, double lambda, double dx)
+int refresh_ghosts(spfm_grid *g, double lambda, double dx, cudaStream_t st)
 {
     double af[6];
     for (int f = 0; f < 6; ++f) {
         const double sgn = (f % 2 == 0) ? -1.0 : 1.0;
         af[f] = tanh(2.0 * sgn * dx * g->d.n[f / 2] / lambda);
     }
-    cudaError_t e = launch_fill_ghosts(g->geom, g->d.dtype, af, g->d.field[g->cur], stream_of(g), 1);
+    cudaError_t e = launch_fill_ghosts(g->geom, g->d.dtype, af, g->d.field[g->cur], st ? st : stream_of(g), 1);
     if (e != cudaSuccess) return cuda_fail(g, e, "ghost fill");
     g->ghosts_dirty = false;
     g->ghost_lambda = lambda;
@@ -189,6 +189,13 @@ int refresh_ghosts(spfm_grid *g, double lambda, double dx)
 // Every face periodic, nx a whole number (>= 2) of 32-byte sectors and ny >= 2:
 // the step kernel writes the ghost images of its new cells itself (kImages),
 // its x images as whole sectors of the row pads.
+bool faces_inline(const spfm_grid *g)
+{
+    for (int f = 0; f < 6; ++f)
+        if (g->d.bc[f] == SPFM_PERIODIC) return false;
+    return true;
+}
+
 bool writes_own_images(const spfm_grid *g)
 {
     for (int f = 0; f < 6; ++f)
@@ -363,7 +370,10 @@ spfm_status spfm_set_rounding(spfm_grid *g, int mode, unsigned long long seed)
 
 int spfm_current(const spfm_grid *g) { return g ? g->cur : -1; }
 
-int spfm_kernels_per_step(const spfm_grid *g) { return g ? (writes_own_images(g) ? 1 : 2) : -1; }
+int spfm_kernels_per_step(const spfm_grid *g)
+{
+    return g ? ((writes_own_images(g) || faces_inline(g)) ? 1 : 2) : -1;
+}
 
 static spfm_status init_common(spfm_grid *g, InitArgs &a, double lambda, double dx)
 {
@@ -427,17 +437,22 @@ spfm_status spfm_step(spfm_grid *g, int n_steps, double M, double Gamma, double 
     if (st != SPFM_OK) return st;
     LaunchCfg cfg{stencil, scheme, 0};
     cudaStream_t s = stream_of(g);
-    if (n_steps > 0 && (g->ghosts_dirty || g->ghost_lambda != lambda || g->ghost_dx != dx)) {
+    // no periodic face: the step kernel computes the ghosts of the faces as it
+    // reads them, and no face kernel runs (the ghost layer in memory is not used)
+    const bool inline_faces = faces_inline(g);
+    if (n_steps > 0 && !inline_faces && (g->ghosts_dirty || g->ghost_lambda != lambda || g->ghost_dx != dx)) {
         st = refresh_ghosts(g, lambda, dx);
         if (st != SPFM_OK) return st;
     }
     // all faces periodic and rows of whole 32-byte sectors: each step writes the
     // periodic images of its new cells, and no face kernel runs between steps
     const bool images = writes_own_images(g);
+    const bool face_kernel = !images && !inline_faces;
     const int skip = g->skip_copy && n_steps > 0 ? kSkipCopy : 0;
     g->skip_copy = g->skip_copy && n_steps == 0;
     auto mode_of = [&](int i) {
-        return (images ? kWaitAll | kImages : (i == 0 ? kWaitAll : kWaitFaces)) | (i == 0 ? skip : 0);
+        const int m = images ? kWaitAll | kImages : (inline_faces ? kWaitAll | kEarly : (i == 0 ? kWaitAll : kWaitFaces));
+        return m | (i == 0 ? skip : 0);
     };
     int *err = err_word(g);
     if (g->d.dtype == SPFM_F64) {
@@ -449,7 +464,7 @@ spfm_status spfm_step(spfm_grid *g, int n_steps, double M, double Gamma, double 
             cudaError_t e = launch_step_f64(c, (const double *)g->d.field[g->cur],
                                             (double *)g->d.field[1 - g->cur], err, cfg, &g->tma,
                                             g->cur, s);
-            if (e == cudaSuccess && !images)
+            if (e == cudaSuccess && face_kernel)
                 e = launch_fill_ghosts(g->geom, g->d.dtype, m.aface, g->d.field[1 - g->cur], s, 1);
             if (e != cudaSuccess) return cuda_fail(g, e, "spfm_step");
             g->cur ^= 1;
@@ -471,12 +486,13 @@ spfm_status spfm_step(spfm_grid *g, int n_steps, double M, double Gamma, double 
                 e = launch_step_bf16(c, (const __nv_bfloat16 *)g->d.field[g->cur],
                                      (__nv_bfloat16 *)g->d.field[1 - g->cur], err, cfg, &g->tma,
                                      g->cur, s);
-            if (e == cudaSuccess && !images)
+            if (e == cudaSuccess && face_kernel)
                 e = launch_fill_ghosts(g->geom, g->d.dtype, m.aface, g->d.field[1 - g->cur], s, 1);
             if (e != cudaSuccess) return cuda_fail(g, e, "spfm_step");
             g->cur ^= 1;
         }
     }
+    if (inline_faces && n_steps > 0) g->ghosts_dirty = true;   // the ghost layer in memory is stale
     g->steps += n_steps;
     g->time += n_steps * dt;
     g->M = M;

@@ -119,6 +119,9 @@ struct spfm_batch {
     std::vector<double> h_finals;
     std::vector<long long> h_steps;
     int sr = 0;   // the grids round their updates stochastically (they share the mode)
+    // no grid has a periodic face: the step kernels compute the ghosts as they
+    // read them and no ghost kernel runs between steps
+    bool inline_faces = false;
     cudaGraphExec_t exec = nullptr;
     int graph_stencil = -1, graph_kind = -1, graph_sr = -1;
     std::string err;
@@ -174,22 +177,24 @@ static cudaError_t launch_one(spfm_batch *b, int parity, int stencil, int kind, 
     int *err = (int *)(b->scratch + b->L.err);
     const long long *steps = (const long long *)(b->scratch + b->L.steps);
     cudaError_t e;
+    const int fwd = b->inline_faces ? 1 : 0;
     if (b->dtype == SPFM_F64) {
-        e = launch_batch_f64(grids, items, b->nitems, parity, err, stencil, kind, b->stream);
+        e = launch_batch_f64(grids, items, b->nitems, parity, err, stencil, kind, b->stream, fwd);
     } else if (b->dtype == SPFM_F32) {
         // the two tile shapes run as two persistent launches over their parts of
         // the list (their grids differ, so the second needs nothing of the first)
         e = cudaSuccess;
         if (b->nitems0 > 0)
             e = launch_batch_f32(grids, items, b->nitems0, parity, err, stencil, kind, b->stream, 0, b->sr, steps,
-                                 sub);
+                                 sub, fwd);
         if (e == cudaSuccess && b->nitems > b->nitems0)
             e = launch_batch_f32(grids, items + b->nitems0, b->nitems - b->nitems0, parity, err, stencil, kind,
-                                 b->stream, 1, b->sr, steps, sub);
+                                 b->stream, 1, b->sr, steps, sub, fwd);
     } else {
-        e = launch_batch_bf16(grids, items, b->nitems, parity, err, stencil, kind, b->stream, b->sr, steps, sub);
+        e = launch_batch_bf16(grids, items, b->nitems, parity, err, stencil, kind, b->stream, b->sr, steps, sub,
+                              fwd);
     }
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || b->inline_faces) return e;
     return launch_fill_ghosts_batch((const GhostJob *)(b->scratch + b->L.ghosts), b->n, b->dtype,
                                     parity ^ 1, b->stream);
 }
@@ -268,6 +273,8 @@ spfm_status spfm_batch_create(spfm_grid *const *grids, int n, void *scratch, siz
     b->scratch = (char *)scratch;
     b->stream = (cudaStream_t)stream;
     b->L = L;
+    b->inline_faces = true;
+    for (int i = 0; i < n; ++i) b->inline_faces = b->inline_faces && faces_inline(grids[i]);
     b->h_grids.assign(grid_record_bytes(dtype) * n, 0);
     b->h_ghosts.resize(n);
     b->h_stats.resize(n);
@@ -309,7 +316,8 @@ spfm_status spfm_batch_step(spfm_batch *b, int n_steps, const spfm_step_args *ar
             snprintf(msg, sizeof msg, "grid %d: %s", i, g->err.c_str());
             return bfail(b, st, msg);
         }
-        if (n_steps > 0 && (g->ghosts_dirty || g->ghost_lambda != a.lambda || g->ghost_dx != a.dx)) {
+        if (n_steps > 0 && !b->inline_faces &&
+            (g->ghosts_dirty || g->ghost_lambda != a.lambda || g->ghost_dx != a.dx)) {
             e = launch_fill_ghosts(g->geom, g->d.dtype, m.aface, g->d.field[g->cur], b->stream, 1);
             if (e != cudaSuccess) return bfail(b, SPFM_ECUDA, cudaGetErrorString(e));
             g->ghosts_dirty = false;
@@ -367,6 +375,7 @@ spfm_status spfm_batch_step(spfm_batch *b, int n_steps, const spfm_step_args *ar
         spfm_grid *g = b->grids[i];
         const spfm_step_args &a = args[i];
         g->cur ^= (n_steps & 1);
+        if (b->inline_faces && n_steps > 0) g->ghosts_dirty = true;   // the ghost layer in memory is stale
         g->steps += n_steps;
         g->time += n_steps * a.dt;
         g->M = a.M;
@@ -487,8 +496,12 @@ spfm_status spfm_batch_stats(spfm_batch *b, int flags, spfm_stats *out)
         if (!(g->lambda > 0.0)) return bfail(b, SPFM_EINVAL, "spfm_batch_stats: a grid has no model yet");
         StatsJob &j = b->h_stats[i];
         fill_stats_args(g, flags, j.a);
-        if (j.a.energy && (g->ghosts_dirty || g->ghost_lambda != g->lambda || g->ghost_dx != g->dx))
-            return bfail(b, SPFM_EINVAL, "spfm_batch_stats: energy needs valid ghosts (step the batch first)");
+        // the energy reads the ghosts: refresh a stale layer (no periodic face:
+        // the steps do not keep it in memory)
+        if (j.a.energy && (g->ghosts_dirty || g->ghost_lambda != g->lambda || g->ghost_dx != g->dx)) {
+            spfm_status st = refresh_ghosts(g, g->lambda, g->dx, b->stream);
+            if (st != SPFM_OK) return bfail(b, st, "spfm_batch_stats: ghost refresh failed");
+        }
         j.field[0] = g->d.field[0];
         j.field[1] = g->d.field[1];
         j.cur = g->cur;

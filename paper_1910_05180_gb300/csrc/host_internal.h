@@ -56,9 +56,14 @@ void default_gamma(int stencil, const double *given, double *g);
 int build_model(spfm_grid *g, double M, double Gamma, double lambda, double dx, double dt,
                 double dF, int stencil, int scheme, Model &m);
 cudaStream_t stream_of(const spfm_grid *g);
-int refresh_ghosts(spfm_grid *g, double lambda, double dx);
+// ghost layer of the current buffer from the interior (face kernel), on st or
+// the grid's stream
+int refresh_ghosts(spfm_grid *g, double lambda, double dx, cudaStream_t st = nullptr);
 int *err_word(const spfm_grid *g);
 bool writes_own_images(const spfm_grid *g);
+// no periodic face: the step kernels compute the ghosts as they read them, and
+// no face kernel runs between steps (the ghost layer in memory goes stale)
+bool faces_inline(const spfm_grid *g);
 void fill_stats_args(const spfm_grid *g, int flags, spfm::StatsArgs &a);
 void stats_from_reduction(const spfm_grid *g, const double *h, int energy, spfm_stats *out);
 

@@ -173,7 +173,10 @@ struct LaunchCfg {
 //               itself (no face kernel follows) and lets the next step launch early
 //   kSkipCopy   test of the bounded waits: the first CTA skips one plane's copy
 //               (spfm_debug_skip_copy), its waits give up and set the error word
-constexpr int kWaitFaces = 1, kWaitAll = 2, kImages = 4, kSkipCopy = 8;
+//   kEarly      no face kernel follows (no periodic face: the step computes the
+//               ghosts of the non-periodic faces as it reads them): the step lets
+//               the next one launch at its start, like the image-writing kernels
+constexpr int kWaitFaces = 1, kWaitAll = 2, kImages = 4, kSkipCopy = 8, kEarly = 16;
 
 // TMA tensor maps of a grid's two field buffers, encoded on first use (tma.cu).
 struct TmaCache {
@@ -292,17 +295,21 @@ void batch_fill_grid_bf16(void *slot, const StepCoef<float> &c, void *const fiel
 // sr: stochastic rounding (the *_sr kernels), whose step keys come from
 // steps[grid] (device: each grid's step count at the start of the call) + sub
 // (the launch's position in the call)
+// fwd: no grid of the batch has a periodic face; the kernel stages the ghosts
+// of the faces and no ghost kernel has to run
 cudaError_t launch_batch_f32(const void *grids, const BatchItem *work, int nwork, int parity, int *err,
                              int stencil, int kind, cudaStream_t st, int shape, int sr, const long long *steps,
-                             int sub);
+                             int sub, int fwd);
 cudaError_t launch_batch_f64(const void *grids, const BatchItem *work, int nwork, int parity, int *err,
-                             int stencil, int kind, cudaStream_t st);
+                             int stencil, int kind, cudaStream_t st, int fwd);
 cudaError_t launch_batch_bf16(const void *grids, const BatchItem *work, int nwork, int parity, int *err,
-                              int stencil, int kind, cudaStream_t st, int sr, const long long *steps, int sub);
+                              int stencil, int kind, cudaStream_t st, int sr, const long long *steps, int sub,
+                              int fwd);
 cudaError_t launch_batch_f32_sr(const void *grids, const BatchItem *work, int nwork, int parity, int *err,
-                                int stencil, int kind, cudaStream_t st, int shape, const long long *steps, int sub);
+                                int stencil, int kind, cudaStream_t st, int shape, const long long *steps, int sub,
+                                int fwd);
 cudaError_t launch_batch_bf16_sr(const void *grids, const BatchItem *work, int nwork, int parity, int *err,
-                                 int stencil, int kind, cudaStream_t st, const long long *steps, int sub);
+                                 int stencil, int kind, cudaStream_t st, const long long *steps, int sub, int fwd);
 // steps[i] += k for the n grids of a batch (after the k steps of a call or graph)
 cudaError_t launch_advance_steps(long long *steps, int n, int k, cudaStream_t st);
 

@@ -42,9 +42,10 @@ void batch_fill_grid_bf16(void *slot, const StepCoef<float> &c, void *const fiel
 
 cudaError_t launch_batch_bf16(const void *grids, const BatchItem *work, int nwork, int parity,
                               int *err, int stencil, int kind, cudaStream_t st, int sr, const long long *steps,
-                              int sub)
+                              int sub, int fwd)
 {
-    if (sr) return launch_batch_bf16_sr(grids, work, nwork, parity, err, stencil, kind, st, steps, sub);
-    return launch_batch_t<__nv_bfloat16, float, kBfTX, kBfTY>(grids, work, nwork, parity, err, stencil, kind, st);
+    if (sr) return launch_batch_bf16_sr(grids, work, nwork, parity, err, stencil, kind, st, steps, sub, fwd);
+    return launch_batch_t<__nv_bfloat16, float, kBfTX, kBfTY>(grids, work, nwork, parity, err, stencil, kind, st,
+                                                               nullptr, 0, fwd);
 }
 }  // namespace spfm

@@ -14,9 +14,9 @@ cudaError_t launch_step_bf16_sr(const StepCoef<float> &c, const __nv_bfloat16 *s
 }
 
 cudaError_t launch_batch_bf16_sr(const void *grids, const BatchItem *work, int nwork, int parity, int *err,
-                                 int stencil, int kind, cudaStream_t st, const long long *steps, int sub)
+                                 int stencil, int kind, cudaStream_t st, const long long *steps, int sub, int fwd)
 {
     return launch_batch_t<__nv_bfloat16, float, kBfTX, kBfTY, false, true>(grids, work, nwork, parity, err,
-                                                                           stencil, kind, st, steps, sub);
+                                                                           stencil, kind, st, steps, sub, fwd);
 }
 }  // namespace spfm

@@ -50,11 +50,13 @@ void batch_fill_grid_f32(void *slot, const StepCoef<float> &c, void *const field
 
 cudaError_t launch_batch_f32(const void *grids, const BatchItem *work, int nwork, int parity,
                               int *err, int stencil, int kind, cudaStream_t st, int shape, int sr,
-                              const long long *steps, int sub)
+                              const long long *steps, int sub, int fwd)
 {
-    if (sr) return launch_batch_f32_sr(grids, work, nwork, parity, err, stencil, kind, st, shape, steps, sub);
+    if (sr) return launch_batch_f32_sr(grids, work, nwork, parity, err, stencil, kind, st, shape, steps, sub, fwd);
     if (shape == 1)
-        return launch_batch_t<float, float, kSqTX, kSqTY, true>(grids, work, nwork, parity, err, stencil, kind, st);
-    return launch_batch_t<float, float, SPFM_F32_TX, SPFM_F32_TY>(grids, work, nwork, parity, err, stencil, kind, st);
+        return launch_batch_t<float, float, kSqTX, kSqTY, true>(grids, work, nwork, parity, err, stencil, kind, st,
+                                                                 nullptr, 0, fwd);
+    return launch_batch_t<float, float, SPFM_F32_TX, SPFM_F32_TY>(grids, work, nwork, parity, err, stencil, kind, st,
+                                                                   nullptr, 0, fwd);
 }
 }  // namespace spfm

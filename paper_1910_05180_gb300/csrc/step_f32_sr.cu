@@ -14,12 +14,13 @@ cudaError_t launch_step_f32_sr(const StepCoef<float> &c, const float *src, float
 }
 
 cudaError_t launch_batch_f32_sr(const void *grids, const BatchItem *work, int nwork, int parity, int *err,
-                                int stencil, int kind, cudaStream_t st, int shape, const long long *steps, int sub)
+                                int stencil, int kind, cudaStream_t st, int shape, const long long *steps, int sub,
+                                int fwd)
 {
     if (shape == 1)
         return launch_batch_t<float, float, kSqTX, kSqTY, true, true>(grids, work, nwork, parity, err, stencil,
-                                                                       kind, st, steps, sub);
+                                                                       kind, st, steps, sub, fwd);
     return launch_batch_t<float, float, SPFM_F32_TX, SPFM_F32_TY, false, true>(grids, work, nwork, parity, err,
-                                                                               stencil, kind, st, steps, sub);
+                                                                               stencil, kind, st, steps, sub, fwd);
 }
 }  // namespace spfm

@@ -39,8 +39,9 @@ void batch_fill_grid_f64(void *slot, const StepCoef<double> &c, void *const fiel
 }
 
 cudaError_t launch_batch_f64(const void *grids, const BatchItem *work, int nwork, int parity,
-                              int *err, int stencil, int kind, cudaStream_t st)
+                              int *err, int stencil, int kind, cudaStream_t st, int fwd)
 {
-    return launch_batch_t<double, double, 16, 16>(grids, work, nwork, parity, err, stencil, kind, st);
+    return launch_batch_t<double, double, 16, 16>(grids, work, nwork, parity, err, stencil, kind, st, nullptr, 0,
+                                                  fwd);
 }
 }  // namespace spfm

@@ -515,6 +515,76 @@ __device__ __forceinline__ void store_z_images(const GridGeom &g, S *dst, int x,
     }
 }
 
+// ------------------------------------------------ ghosts of non-periodic faces
+
+// Ghost value of a non-periodic face from its source cell v: the
+// contact-angle value of Eq. 7 with the face's signed coupling a,
+// (1 - a) v / (1 - a (2 v - 1)) = k1 v / (k2 - k3 v), or a copy (no-flux).
+// FP32 takes the approximate reciprocal (the face kernel divides exactly, so
+// the two differ in the last unit; the ghosts are not kept in memory here).
+template <class T> struct FaceMap {
+    T k1, k2, k3;
+    bool copy;
+};
+template <class T>
+__device__ __forceinline__ FaceMap<T> face_map(int bc, T a)
+{
+    return FaceMap<T>{T(1) - a, T(1) + a, T(2) * a, bc != SPFM_CONTACT};
+}
+__device__ __forceinline__ float face_value(float v, const FaceMap<float> &m)
+{
+    if (m.copy) return v;
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(__fmaf_rn(-m.k3, v, m.k2)));
+    return m.k1 * v * r;
+}
+__device__ __forceinline__ double face_value(double v, const FaceMap<double> &m)
+{
+    return m.copy ? v : m.k1 * v / (m.k2 - m.k3 * v);
+}
+
+// The staged plane st (ROWS x SW, the tile plus halo) of a grid whose faces
+// are all non-periodic gets the ghost values of the faces it touches, from the
+// interior cells next to them, in the face kernel's order: the x ghost columns
+// of every row, then the y ghost rows (x ghosts included).  Run by the 32
+// lanes of the producer warp; no face kernel then runs between steps.
+template <class S, class T, int VX, int SW, int ROWS>
+__device__ __forceinline__ void fix_xy(S *st, const GridGeom &g, const T *aface, int x0, int y0, int W, int TY,
+                                       int lane)
+{
+    const bool xlo = x0 == 0;
+    const int xhi = (g.nx - 1 >= x0 && g.nx - 1 < x0 + W) ? g.nx - x0 + VX : -1;   // column of x = nx
+    const bool ylo = y0 == 0;
+    const int yhi = (g.ny - 1 >= y0 && g.ny - 1 < y0 + TY) ? g.ny - y0 + 1 : -1;    // row of y = ny
+    if (xlo || xhi >= 0) {
+        const FaceMap<T> ml = face_map<T>(g.bc[0], aface[0]), mh = face_map<T>(g.bc[1], aface[1]);
+        for (int k = lane; k < ROWS; k += 32) {
+            S *row = st + k * SW;
+            if (xlo) row[VX - 1] = Io<S, T>::cvt_out(face_value(Io<S, T>::cvt_in(row[VX]), ml));
+            if (xhi >= 0) row[xhi] = Io<S, T>::cvt_out(face_value(Io<S, T>::cvt_in(row[xhi - 1]), mh));
+        }
+        __syncwarp();
+    }
+    if (ylo) {
+        const FaceMap<T> m = face_map<T>(g.bc[2], aface[2]);
+        for (int c = lane; c < SW; c += 32) st[c] = Io<S, T>::cvt_out(face_value(Io<S, T>::cvt_in(st[SW + c]), m));
+    }
+    if (yhi >= 0) {
+        const FaceMap<T> m = face_map<T>(g.bc[3], aface[3]);
+        for (int c = lane; c < SW; c += 32)
+            st[yhi * SW + c] = Io<S, T>::cvt_out(face_value(Io<S, T>::cvt_in(st[(yhi - 1) * SW + c]), m));
+    }
+}
+
+// A z ghost plane (plane -1 or nz) staged from its adjacent interior plane
+// (already carrying its x and y ghosts): every value shifted by the z face.
+template <class S, class T, int SW, int ROWS>
+__device__ __forceinline__ void fix_z(S *dst, const S *src, const GridGeom &g, const T *aface, int face, int lane)
+{
+    const FaceMap<T> m = face_map<T>(g.bc[face], aface[face]);
+    for (int i = lane; i < ROWS * SW; i += 32) dst[i] = Io<S, T>::cvt_out(face_value(Io<S, T>::cvt_in(src[i]), m));
+}
+
 // KIND: 0 = CF potential; 1..4 = TI global with exactly KIND coupling groups;
 // 5 = TI global with up to 13 groups (count read at run time)
 // One tile (bx, by) of planes zc0..zc1-1.  The stage ring continues across the
@@ -529,7 +599,8 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
                                           int *__restrict__ err, const CUtensorMap *tmap, int bx,
                                           int by, int zc0, int zc1, S *__restrict__ stages,
                                           uint64_t *full, uint64_t *empty, int base, bool drain,
-                                          int mode = 0, uint32_t sr_key = 0)
+                                          int mode = 0, uint32_t sr_key = 0, uint64_t *ready = nullptr,
+                                          bool fwd = false)
 {
     static_assert(!SR || sizeof(T) == 4, "stochastic rounding is for FP32 compute");
     using Sh = TileShape<S, T, TX, TY, RPT_>;
@@ -547,48 +618,96 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
 
     if (tid >= Sh::NCONS) {
         // ------------------------------------------------------- producer warp
-        if (tid != Sh::NCONS) return true;
+        // fwd (every face non-periodic): the whole warp builds the ghosts of the
+        // faces a staged plane touches (fix_xy, fix_z) and then releases it to
+        // the consumers on its "ready" barrier, NS - 2 planes behind the copies,
+        // so that as many copies stay in flight; otherwise one lane issues the
+        // copies and the consumers wait on "full".
+        const int plane_lane = tid - Sh::NCONS;
+        if (!fwd && plane_lane != 0) return true;
+        const bool lead = plane_lane == 0;
         // The kernel may start while the previous launch still runs (programmatic
         // dependent launch).  After a ghost-face refresh of src, a box that holds
         // no ghost cell reads only interior cells, which the step before that
         // wrote, so only boxes touching a face wait for the previous grid; after
         // anything else (a step that wrote its own images, the first step of a
         // call) every box waits.
-        if ((mode & kWaitAll) ||
-            ((mode & kWaitFaces) &&
-             (bx == 0 || x0 + W >= g.nx || by == 0 || y0 + TY >= g.ny || zc0 == 0 || zc1 == g.nz)))
+        if (lead && ((mode & kWaitAll) ||
+                     ((mode & kWaitFaces) &&
+                      (bx == 0 || x0 + W >= g.nx || by == 0 || y0 + TY >= g.ny || zc0 == 0 || zc1 == g.nz))))
             asm volatile("griddepcontrol.wait;" ::: "memory");
         // kSkipCopy (a test of the bounded waits): the first CTA never fills the
         // stage of its plane 1, so its consumers' wait for that stage gives up
         const bool skip = (mode & kSkipCopy) && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0;
+        const bool zlo = fwd && zc0 == 0, zhi = fwd && zc1 == g.nz;
+        auto stage = [&](int j) { return stages + ((base + j) % NS) * STAGE; };
+        // waits on the forwarding path suspend in hardware until the phase
+        // completes (no sleep back-off: the consumers wait behind them)
+        auto wait_full = [&](int j) {
+            return __all_sync(0xffffffffu, mbar_wait(&full[(base + j) % NS], ((base + j) / NS) & 1));
+        };
+        auto release = [&](int j) {
+            __syncwarp();
+            if (lead) mbar_arrive(&ready[(base + j) % NS]);
+        };
+        // plane j to the consumers: its x/y ghosts, or (a z ghost plane) all of it
+        // from the adjacent interior plane; plane 0 of a z- face follows plane 1
+        auto forward = [&](int j) -> bool {
+            if (zlo && j == 0) return true;
+            if (!wait_full(j)) return false;
+            if (zhi && j == nplanes - 1) fix_z<S, T, SW, ROWS>(stage(j), stage(j - 1), g, C.aface, 5, plane_lane);
+            else fix_xy<S, T, VX, SW, ROWS>(stage(j), g, C.aface, x0, y0, W, TY, plane_lane);
+            release(j);
+            if (zlo && j == 1) {
+                if (!wait_full(0)) return false;
+                fix_z<S, T, SW, ROWS>(stage(0), stage(1), g, C.aface, 4, plane_lane);
+                release(0);
+            }
+            return true;
+        };
+        // lag NS - 2: plane 0 of a z- face, forwarded with plane 1, is released
+        // before the copy of plane NS has to wait for its stage
+        const int lag = fwd ? NS - 2 : 0;
         int issued = 0;
         bool ok = true;
-        for (int i = 0; i < nplanes; ++i) {
-            const int I = base + i, s = I % NS;
-            if (I >= NS && !mbar_wait_sleep(&empty[s], ((I / NS) - 1) & 1)) { ok = false; break; }
-            if (skip && i == 1) {
-                ++issued;
-                continue;
+        for (int i = 0; i < nplanes + lag; ++i) {
+            if (i < nplanes) {
+                if (lead) {
+                    const int I = base + i, s = I % NS;
+                    if (I >= NS && !(fwd ? mbar_wait(&empty[s], ((I / NS) - 1) & 1)
+                                         : mbar_wait_sleep(&empty[s], ((I / NS) - 1) & 1))) {
+                        ok = false;
+                    } else if (!(skip && i == 1)) {
+                        if (tmap) {
+                            mbar_expect_tx(&full[s], (uint32_t)Sh::BOX_BYTES);
+                            // one box: padded x from the 16-byte chunk left of the tile (x0 + off
+                            // - VX, 16-byte aligned), padded rows y0.., padded plane zc0 + i;
+                            // out-of-range parts are zero-filled, never used
+                            tma_load_3d(stages + s * STAGE, tmap, x0 + g.off - VX, y0, zc0 + i, &full[s]);
+                        } else {
+                            // row by row (no tensor map): the box's rows that lie in the buffer
+                            const long long row0 = (long long)(x0 + g.off - VX);
+                            const int bytes_row = (int)min((long long)SW, (long long)g.pitch - row0) * (int)sizeof(S);
+                            const int nrows = min(ROWS, g.ny + 2 - y0);
+                            mbar_expect_tx(&full[s], (uint32_t)(bytes_row * nrows));
+                            const S *plane = src + (long long)(zc0 + i) * g.plane + (long long)y0 * g.pitch + row0;
+                            S *st = stages + s * STAGE;
+                            for (int r = 0; r < nrows; ++r)
+                                bulk_g2s(st + r * SW, plane + (long long)r * g.pitch, (uint32_t)bytes_row, &full[s]);
+                        }
+                    }
+                    if (ok) ++issued;
+                }
+                if (fwd) ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
+                if (!ok) break;
             }
-            if (tmap) {
-                mbar_expect_tx(&full[s], (uint32_t)Sh::BOX_BYTES);
-                // one box: padded x from the 16-byte chunk left of the tile (x0 + off
-                // - VX, 16-byte aligned), padded rows y0.., padded plane zc0 + i;
-                // out-of-range parts are zero-filled, never used
-                tma_load_3d(stages + s * STAGE, tmap, x0 + g.off - VX, y0, zc0 + i, &full[s]);
-            } else {
-                // row by row (no tensor map): the box's rows that lie in the buffer
-                const long long row0 = (long long)(x0 + g.off - VX);
-                const int bytes_row = (int)min((long long)SW, (long long)g.pitch - row0) * (int)sizeof(S);
-                const int nrows = min(ROWS, g.ny + 2 - y0);
-                mbar_expect_tx(&full[s], (uint32_t)(bytes_row * nrows));
-                const S *plane = src + (long long)(zc0 + i) * g.plane + (long long)y0 * g.pitch + row0;
-                S *st = stages + s * STAGE;
-                for (int r = 0; r < nrows; ++r)
-                    bulk_g2s(st + r * SW, plane + (long long)r * g.pitch, (uint32_t)bytes_row, &full[s]);
+            if (fwd && i >= lag && !forward(i - lag)) {
+                ok = false;
+                break;
             }
-            ++issued;
         }
+        if (fwd) issued = __shfl_sync(0xffffffffu, issued, 0);
+        if (!lead) return ok;
         if (!ok) atomicOr(err, 1);
         // never leave with copies in flight: wait for each stage's copy (a stage
         // whose wait gives up does not stop the waits for the others)
@@ -625,7 +744,7 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
                     PlaneQ<T, NP> (&p)[RPT]) -> bool {
         const int I = base + i, s = I % NS;
         // warp-uniform: every lane waits (acquire), the warp goes on only if all saw it
-        if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (I / NS) & 1))) {
+        if (!__all_sync(0xffffffffu, mbar_wait(fwd ? &ready[s] : &full[s], (I / NS) & 1))) {
             if (lane == 0) atomicOr(err, 4);
             ok = false;
             return false;
@@ -853,34 +972,44 @@ template <class S> struct MinBlocks { static constexpr int value = SPFM_MIN_CTAS
 template <> struct MinBlocks<float> { static constexpr int value = 4; };
 template <class S> struct BatchMinBlocks { static constexpr int value = SPFM_MIN_CTAS; };
 
-// (the stochastic-rounding kernels keep three CTAs per SM: at four their extra
-// registers spill)
+// (the stochastic-rounding kernels and the 13-group potential keep three CTAs
+// per SM: at four their registers spill, and the 13-group kernel ran 15-18 %
+// slower at 192^3)
 template <class S, class T, int STENCIL, int KIND, int TX, int TY, int RPT_, bool IMG, bool SR = false>
 __global__ void __launch_bounds__(TileShape<S, T, TX, TY, RPT_>::NTHREADS,
-                                  RPT_ == 1 ? 2 : (SR ? SPFM_MIN_CTAS : MinBlocks<S>::value))
+                                  RPT_ == 1 ? 2 : ((SR || KIND == 5) ? SPFM_MIN_CTAS : MinBlocks<S>::value))
     spfm_step_kernel(const StepCoef<T> C, const PackCoef<T> PC, const S *__restrict__ src,
                      S *__restrict__ dst, int *__restrict__ err, int zchunk,
                      const __grid_constant__ CUtensorMap tmap, int use_tmap, int mode)
 {
     using Sh = TileShape<S, T, TX, TY, RPT_>;
-    // a step that writes its own ghost images lets the next step launch at once:
-    // every box of that step waits for this grid (kWaitAll) before it reads
-    if constexpr (IMG) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    // a step that writes its own ghost images, or whose grid has no periodic face
+    // (no face kernel follows), lets the next step launch at once: every box of
+    // that step waits for this grid (kWaitAll) before it reads
+    if (IMG || (mode & kEarly)) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     __shared__ __align__(128) S stages[Sh::NS * Sh::STAGE];
-    __shared__ __align__(8) uint64_t full[Sh::NS], empty[Sh::NS];
+    __shared__ __align__(8) uint64_t full[Sh::NS], empty[Sh::NS], ready[Sh::NS];
     if (threadIdx.x == 0) {
         for (int s = 0; s < Sh::NS; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], Sh::NCONS / 32);
+            mbar_init(&ready[s], 1);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     const int zc0 = blockIdx.z * zchunk;
     const int zc1 = min(zc0 + zchunk, C.g.nz);
+    // no periodic face: the producer warp stages the ghosts of the faces
+    bool fwd = false;
+    if constexpr (!IMG) {
+        fwd = true;
+#pragma unroll
+        for (int f = 0; f < 6; ++f) fwd = fwd && C.g.bc[f] != SPFM_PERIODIC;
+    }
     step_tile<S, T, STENCIL, KIND, TX, TY, RPT_, IMG, SR>(C, PC, src, dst, err, use_tmap ? &tmap : nullptr,
                                                      blockIdx.x, blockIdx.y, zc0, zc1, stages, full, empty, 0,
-                                                     true, mode, C.sr_key);
+                                                     true, mode, C.sr_key, ready, fwd);
 }
 
 // ------------------------------------------------------------------- batches
@@ -902,20 +1031,22 @@ struct BatchGrid {
 // TY): CTA b takes items b, b + gridDim.x, ...  Step `parity` reads buffer
 // cur ^ parity.  SQ: the items use the square tile's TMA maps (map_sq).
 // SR: stochastic rounding, the step key of grid i from sr_step_key(its seed,
-// steps[i] + sub).
+// steps[i] + sub).  fwd: no grid of the batch has a periodic face (the
+// producer warp stages the ghosts of the faces; no ghost kernel runs).
 template <class S, class T, int STENCIL, int KIND, int TX, int TY, bool SQ, bool SR = false>
 __global__ void __launch_bounds__(TileShape<S, T, TX, TY>::NTHREADS, BatchMinBlocks<S>::value)
     spfm_batch_kernel(const BatchGrid<T> *__restrict__ grids, const BatchItem *__restrict__ work,
                       int nwork, int parity, int *__restrict__ err, const long long *__restrict__ steps,
-                      int sub)
+                      int sub, int fwd)
 {
     using Sh = TileShape<S, T, TX, TY>;
     __shared__ __align__(128) S stages[Sh::NS * Sh::STAGE];
-    __shared__ __align__(8) uint64_t full[Sh::NS], empty[Sh::NS];
+    __shared__ __align__(8) uint64_t full[Sh::NS], empty[Sh::NS], ready[Sh::NS];
     if (threadIdx.x == 0) {
         for (int s = 0; s < Sh::NS; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], Sh::NCONS / 32);
+            mbar_init(&ready[s], 1);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -932,7 +1063,7 @@ __global__ void __launch_bounds__(TileShape<S, T, TX, TY>::NTHREADS, BatchMinBlo
         const uint32_t key = SR ? sr_step_key(bg.C.sr_seed, steps[it.grid] + sub) : 0u;
         if (!step_tile<S, T, STENCIL, KIND, TX, TY, SPFM_ROWS_PER_THREAD, false, SR>(
                 bg.C, bg.PC, (const S *)bg.field[cur], (S *)bg.field[cur ^ 1], err, map, it.bx, it.by, it.zc0,
-                it.zc1, stages, full, empty, base, last, 0, key))
+                it.zc1, stages, full, empty, base, last, 0, key, ready, fwd != 0))
             return;
         base += it.zc1 - it.zc0 + 2;
     }
@@ -958,7 +1089,7 @@ inline int batch_items_t(const GridGeom &g, int grid_index, int zchunk, BatchIte
 template <class S, class T, int TX, int TY, bool SQ = false, bool SR = false>
 cudaError_t launch_batch_t(const void *grids, const BatchItem *work, int nwork, int parity, int *err,
                            int stencil, int kind, cudaStream_t st, const long long *steps = nullptr,
-                           int sub = 0)
+                           int sub = 0, int fwd = 0)
 {
     using Sh = TileShape<S, T, TX, TY>;
     int dev = 0, sms = 152;
@@ -970,7 +1101,7 @@ cudaError_t launch_batch_t(const void *grids, const BatchItem *work, int nwork, 
     const BatchGrid<T> *bg = (const BatchGrid<T> *)grids;
 #define SPFM_BLAUNCH(ST, KD)                                                                               \
     spfm_batch_kernel<S, T, ST, KD, TX, TY, SQ, SR><<<ctas, Sh::NTHREADS, 0, st>>>(bg, work, nwork, parity, err, \
-                                                                                 steps, sub)
+                                                                                 steps, sub, fwd)
 #define SPFM_BBY_KIND(ST)                      \
     do {                                       \
         if (kind == 0) SPFM_BLAUNCH(ST, 0);    \

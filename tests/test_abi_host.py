@@ -74,18 +74,22 @@ def _fake_grid(lib, **kw):
 
 
 def test_kernels_per_step_follows_the_periodic_image_rule(lib):
-    """One launch per step (the step writes its own periodic ghost images) only
-    with every face periodic, nx a whole number (>= 2) of 32-byte sectors and
-    ny >= 2; otherwise the ghost-face kernel follows each step."""
+    """One launch per step when the step writes its own periodic ghost images
+    (every face periodic, nx a whole number (>= 2) of 32-byte sectors, ny >= 2)
+    or when no face is periodic (the step computes the contact and no-flux
+    ghosts as it reads them); otherwise the ghost-face kernel follows each
+    step."""
     P, C = (S.SPFM_PERIODIC,) * 6, (S.SPFM_CONTACT,) * 6
     mixed = (S.SPFM_PERIODIC,) * 4 + (S.SPFM_NOFLUX,) * 2
+    closed = (S.SPFM_NOFLUX,) * 2 + (S.SPFM_CONTACT,) * 4
     cases = [
         (dict(nx=16, ny=2, nz=1, dtype=S.SPFM_F32, bc=P), 1),
         (dict(nx=512, ny=512, nz=512, dtype=S.SPFM_F32, bc=P), 1),
         (dict(nx=8, ny=5, nz=5, dtype=S.SPFM_F32, bc=P), 2),      # one sector only
         (dict(nx=20, ny=5, nz=5, dtype=S.SPFM_F32, bc=P), 2),     # not whole sectors
         (dict(nx=16, ny=1, nz=5, dtype=S.SPFM_F32, bc=P), 2),     # ny = 1
-        (dict(nx=16, ny=5, nz=5, dtype=S.SPFM_F32, bc=C), 2),
+        (dict(nx=16, ny=5, nz=5, dtype=S.SPFM_F32, bc=C), 1),
+        (dict(nx=7, ny=1, nz=3, dtype=S.SPFM_F64, bc=closed), 1),
         (dict(nx=16, ny=5, nz=5, dtype=S.SPFM_F32, bc=mixed), 2),
         (dict(nx=8, ny=5, nz=5, dtype=S.SPFM_F64, bc=P), 1),
         (dict(nx=4, ny=5, nz=5, dtype=S.SPFM_F64, bc=P), 2),

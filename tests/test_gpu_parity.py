@@ -95,6 +95,13 @@ CASES = [
     ((136, 3, 1), (S.SPFM_PERIODIC,) * 6, 18, S.SPFM_TI_LOCAL),
     ((4, 5, 6), (S.SPFM_PERIODIC,) * 6, 26, S.SPFM_TI_GLOBAL),   # images in FP64 only
     ((16, 1, 7), (S.SPFM_PERIODIC,) * 6, 6, S.SPFM_FD_H5),
+    # no periodic face: the step computes the contact and no-flux ghosts as it
+    # reads them (x ghosts inside a chunk, one-row and one-plane grids, TI_n)
+    ((45, 23, 21), (S.SPFM_CONTACT,) * 6, 26, S.SPFM_TI_LOCAL),
+    ((6, 2, 2), (S.SPFM_NOFLUX, S.SPFM_CONTACT, S.SPFM_CONTACT, S.SPFM_NOFLUX, S.SPFM_CONTACT, S.SPFM_CONTACT),
+     26, S.SPFM_TI_GLOBAL),
+    ((33, 17, 1), (S.SPFM_CONTACT,) * 6, 18, S.SPFM_FD),
+    ((70, 1, 3), (S.SPFM_CONTACT,) * 4 + (S.SPFM_NOFLUX,) * 2, 26, S.SPFM_TI_GLOBAL),
 ]
 
 
@@ -208,7 +215,10 @@ def test_ghost_layer_matches_the_face_rule_exactly(dtype, shape, bc):
     """After every step the whole ghost layer (faces, edges, corners) holds the
     face rule applied to the interior, bit for bit: periodic, no-flux and
     contact faces in every combination (the face kernel), and all-periodic
-    rows of whole 32-byte sectors (the step kernel's images)."""
+    rows of whole 32-byte sectors (the step kernel's images).  A grid with no
+    periodic face keeps no ghost layer in memory between steps (the step
+    computes those ghosts as it reads them); an energy stats call, which reads
+    the ghosts, refreshes it first."""
     nx, ny, nz = shape
     n = rng_normal(43)
     lam = 2.5
@@ -216,8 +226,13 @@ def test_ghost_layer_matches_the_face_rule_exactly(dtype, shape, bc):
     rng = np.random.default_rng(44)
     phi0 = O.init_planar(p, float(n @ (np.array(shape) - 1) / 2.0)) + 0.01 * rng.random(p.shape)
     upload(g, phi0, dtype)
+    inline = S.SPFM_PERIODIC not in bc
+    if inline:
+        assert g.kernels_per_step() == 1
     for steps in (1, 2, 5):
         g.step(steps, lam=lam, dt=0.05, dF=0.03, stencil=26)
+        if inline:
+            g.stats(S.SPFM_STATS_ENERGY)
         full = g.current_with_ghosts().double().cpu().numpy()
         want = _ghosted_reference(full[1:-1, 1:-1, 1:-1], bc, n, lam, 1.0, dtype).astype(np.float64)
         bad = np.argwhere(full != want)
