@@ -249,6 +249,21 @@ class ClockSampler:
         return self.summarise(rows, in_window)
 
 
+def issue_ceiling(dev, warp_inst_per_cell: float) -> float:
+    """Cell updates/s at the full issue rate: SMs x 4 schedulers x the maximum
+    SM clock (MEASURED_PEAKS.json, else 2070 MHz) warp instructions per
+    second over the warp instructions one cell update takes."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    except (OSError, ValueError):
+        pass
+    return sms * 4 * mhz * 1e6 / warp_inst_per_cell
+
+
 def measured_hbm_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -989,11 +1004,15 @@ def run_gpu(args):
             variants[name] = {"cell_updates_per_s": cells / (ms / 1e3), "ms_per_step": ms,
                               "frac_hbm": cells * bpu / (ms / 1e3) / 1e9 / peak}
             if sch == S.SPFM_TI_LOCAL:
-                # TI_n is bound by instruction issue: its ceiling from the committed
-                # capture (warp instructions per update at the full issue rate)
-                ceil = profiled_record(f"spfm_step_kernel_{args.dtype}_27pt_local", "alu_ceiling_cell_updates_per_s")
+                # TI_n is bound by instruction issue: its ceiling is the issue rate of
+                # the GPU (SMs x 4 schedulers x the maximum SM clock, one warp
+                # instruction each per cycle) over the warp instructions per cell
+                # update of the committed capture
+                wipc = profiled_record(f"spfm_step_kernel_{args.dtype}_27pt_local", "warp_inst_per_cell")
+                ceil = issue_ceiling(dev, wipc) if wipc else None
                 variants[name]["bound"] = "alu"
-                variants[name]["alu_ceiling_cell_updates_per_s"] = ceil
+                variants[name]["warp_inst_per_cell"] = wipc
+                variants[name]["issue_ceiling_cell_updates_per_s"] = ceil
                 variants[name]["frac_alu"] = cells / (ms / 1e3) / ceil if ceil else None
         leg("variants", variants)
 

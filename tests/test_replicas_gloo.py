@@ -88,12 +88,12 @@ def test_profiled_figures_only_for_the_captured_sources(monkeypatch, tmp_path):
     key = "spfm_step_kernel_f32_27pt_ti120_512"
     rec = {key: {"source_hash": bench.source_hash(), "bytes_per_launch": 1.0e9},
            "spfm_step_kernel_f32_27pt_local": {"source_hash": bench.source_hash(),
-                                               "alu_ceiling_cell_updates_per_s": 2.0e11}}
+                                               "warp_inst_per_cell": 5.8}}
     path = tmp_path / "traffic.json"
     path.write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "TRAFFIC_PATH", str(path))
     assert bench.profiled_traffic(key) == 1.0e9
-    assert bench.profiled_record("spfm_step_kernel_f32_27pt_local", "alu_ceiling_cell_updates_per_s") > 0
+    assert bench.profiled_record("spfm_step_kernel_f32_27pt_local", "warp_inst_per_cell") == 5.8
     assert bench.profiled_traffic("no_such_kernel") is None
     monkeypatch.setattr(bench, "source_hash", lambda names=None: "0000000000000000")
     assert bench.profiled_traffic(key) is None
