@@ -766,6 +766,7 @@ def tilted_256(dev, steps: int = 50, window: int = 400):
                 v = (p2 - p1) / (window * w["dt"])
                 out[f"{sname}_{dname}"] = {"cell_updates_per_s": cells / (ms / 1e3), "ms_per_step": ms,
                                            "frac_hbm": cells * bpu / (ms / 1e3) / 1e9 / peak,
+                                           "zchunk": g.last_zchunk(),
                                            "velocity_rel_err_vs_v_th": abs(v / (-w["dF"]) - 1.0)}
                 g.close()
     out["workload"] = w["name"] + "_contact_27pt"

@@ -141,6 +141,18 @@ spfm_status spfm_set_stream(spfm_grid *g, void *stream);
  * batch must share the mode.  Costs about 11 instructions per cell update. */
 spfm_status spfm_set_rounding(spfm_grid *g, int mode, unsigned long long seed);
 
+/* Planes of the z-march each CTA of a step launch takes (a tuning knob; the
+ * paper has no counterpart).  0 (the default) chooses per launch from the
+ * kernel's occupancy and the grid's shape; a value above nz acts as nz.  The
+ * field is bit for bit the same for every choice.  SPFM_EINVAL for
+ * zchunk < 0.  Takes effect at the next step (spfm_step and
+ * spfm_step_conserving; a batch uses its own depth). */
+spfm_status spfm_set_zchunk(spfm_grid *g, int zchunk);
+
+/* Planes per CTA of the grid's last step launch (0 before the first step;
+ * -1 for a NULL grid). */
+int spfm_last_zchunk(const spfm_grid *g);
+
 /* Test hook of the failure reporting (the paper has no counterpart): the next
  * spfm_step launch skips the copy of one plane in its first CTA, whose bounded
  * waits (about 2 s each) then give up; the kernel returns without writing that
@@ -182,7 +194,8 @@ spfm_status spfm_step(spfm_grid *g, int n_steps, double M, double Gamma, double 
  * which is dF = alpha lambda Gamma / (4 M dt) in the driving term of Eq. 2.
  * Validation as spfm_step at dF = 0 (the phase-stability check of Sec. 3.1
  * cannot see a dF decided during the run); schemes with h3 only (SPFM_EINVAL
- * for SPFM_FD_H5 and SPFM_FD_HABEL).  Uses the grid's scratch.
+ * for SPFM_FD_H5 and SPFM_FD_HABEL).  Uses the grid's scratch.  The step
+ * rounds as spfm_set_rounding sets; the correction rounds to nearest.
  * dF_last (host pointer or NULL) receives the last step's dF; a non-NULL
  * dF_last synchronises the stream. */
 spfm_status spfm_step_conserving(spfm_grid *g, int n_steps, double M, double Gamma, double lambda,

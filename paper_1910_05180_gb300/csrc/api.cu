@@ -368,6 +368,16 @@ spfm_status spfm_set_rounding(spfm_grid *g, int mode, unsigned long long seed)
     return SPFM_OK;
 }
 
+spfm_status spfm_set_zchunk(spfm_grid *g, int zchunk)
+{
+    if (!g) return fail(nullptr, SPFM_EINVAL, "spfm_set_zchunk: grid is NULL");
+    if (zchunk < 0) return fail(g, SPFM_EINVAL, "spfm_set_zchunk: zchunk %d < 0", zchunk);
+    g->zchunk = zchunk;
+    return SPFM_OK;
+}
+
+int spfm_last_zchunk(const spfm_grid *g) { return g ? g->last_zchunk : -1; }
+
 int spfm_current(const spfm_grid *g) { return g ? g->cur : -1; }
 
 int spfm_kernels_per_step(const spfm_grid *g)
@@ -436,6 +446,8 @@ spfm_status spfm_step(spfm_grid *g, int n_steps, double M, double Gamma, double 
     spfm_status st = build_model(g, M, Gamma, lambda, dx, dt, dF, stencil, scheme, m);
     if (st != SPFM_OK) return st;
     LaunchCfg cfg{stencil, scheme, 0};
+    cfg.zchunk = g->zchunk;
+    cfg.zchunk_used = &g->last_zchunk;
     cudaStream_t s = stream_of(g);
     // no periodic face: the step kernel computes the ghosts of the faces as it
     // reads them, and no face kernel runs (the ghost layer in memory is not used)
@@ -516,6 +528,8 @@ spfm_status spfm_step_conserving(spfm_grid *g, int n_steps, double M, double Gam
     spfm_status st = build_model(g, M, Gamma, lambda, dx, dt, 0.0, stencil, scheme, m);
     if (st != SPFM_OK) return st;
     LaunchCfg cfg{stencil, scheme, 0};
+    cfg.zchunk = g->zchunk;
+    cfg.zchunk_used = &g->last_zchunk;
     cudaStream_t s = stream_of(g);
     if (n_steps > 0 && (g->ghosts_dirty || g->ghost_lambda != lambda || g->ghost_dx != dx)) {
         st = refresh_ghosts(g, lambda, dx);
@@ -532,10 +546,12 @@ spfm_status spfm_step_conserving(spfm_grid *g, int n_steps, double M, double Gam
     } else {
         fill_coef<float>(g, m, dt, stencil, cf);
         set_local_coef<float>(cf, lambda, dx);
+        cfg.rounding = g->rounding;
     }
     for (int i = 0; i < n_steps; ++i) {
         void *src = g->d.field[g->cur], *dst = g->d.field[1 - g->cur];
         cfg.mode = i == 0 ? kWaitAll : kWaitFaces;   // the face kernel follows the correction
+        cf.sr_key = sr_step_key(g->sr_seed, g->steps + i);
         cudaError_t e;
         if (g->d.dtype == SPFM_F64)
             e = launch_step_f64(cd, (const double *)src, (double *)dst, err, cfg, &g->tma, g->cur, s);

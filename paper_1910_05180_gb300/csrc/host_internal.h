@@ -24,6 +24,8 @@ struct spfm_grid {
     int rounding = SPFM_ROUND_NEAREST;
     uint32_t sr_seed = 0;
     bool skip_copy = false;   // spfm_debug_skip_copy: the next step launch skips one copy
+    int zchunk = 0;           // spfm_set_zchunk: planes per CTA of the step launches (0: chosen per launch)
+    int last_zchunk = 0;      // planes per CTA of the last step launch
     std::string err;
 };
 
@@ -100,13 +102,13 @@ void fill_coef(const spfm_grid *g, const Model &m, double dt, int stencil, spfm:
     c.sr_seed = g->sr_seed;
 }
 
-// TI_n constants of the step kernels: lambda/2, 1/(2 dx), 2 dx/lambda and the
-// clamp of phi before the profile inversion (1e-6)
+// TI_n constants of the step kernels: the gradient scale of the log-odds
+// (psi = (lambda/4) ln((1 - phi)/phi); the FP32 kernels take log2), 2 dx/lambda
+// and the clamp of phi before the profile inversion (1e-6)
 template <class T>
 void set_local_coef(spfm::StepCoef<T> &c, double lambda, double dx)
 {
-    c.half_lam = (T)(0.5 * lambda);
-    c.inv_2dx = (T)(1.0 / (2.0 * dx));
+    c.psi_grad = (T)(0.25 * lambda * (sizeof(T) == 4 ? 0.69314718055994530942 : 1.0) / (2.0 * dx));
     c.two_dx_over_lam = (T)(2.0 * dx / lambda);
     c.eps = (T)1e-6;
 }

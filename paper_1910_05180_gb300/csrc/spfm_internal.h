@@ -75,9 +75,12 @@ struct StepCoef {
     // t = (phi_{z-1} - phi) + (phi_{z+1} - phi), -beta dt, -kmu dt, -kappa dt
     T c1dt, c2dt, c3dt, ctdt, nkmudt, nkapdt;
     T nbetadt[kMaxTerms];
-    // TI_n (local normal): per-direction c_k, (lambda/2), 1/(2 dx), 2 dx/lambda, clamp
+    // TI_n (local normal): per-direction c_k; the scale that turns a central
+    // difference of the kernels' log-odds ln or log2((1 - phi)/phi) into the
+    // gradient of psi (FP32: (lambda/4) ln 2 / (2 dx), FP64: (lambda/4) / (2 dx));
+    // 2 dx/lambda; the clamp of phi
     T ck[kMaxTerms];
-    T half_lam, inv_2dx, two_dx_over_lam, eps;
+    T psi_grad, two_dx_over_lam, eps;
     // CF models: interpolation function of the driving term, 0 h3, 1 h5, 2 h_Abel
     int interp;
     // stochastic rounding of the update (SPFM_ROUND_STOCHASTIC): the grid's mixed
@@ -164,7 +167,14 @@ struct LaunchCfg {
     int scheme;    // SPFM_TI_GLOBAL, SPFM_TI_LOCAL, SPFM_FD
     int mode;      // kWaitFaces | kWaitAll | kImages
     int rounding = SPFM_ROUND_NEAREST;   // SPFM_ROUND_STOCHASTIC: the *_sr kernels
+    int zchunk = 0;   // planes per CTA; 0: pick_zchunk
+    int *zchunk_used = nullptr;   // receives the planes per CTA of the launch (host, optional)
 };
+
+// Planes per CTA of a step launch of `tiles` xy tiles over nz planes by kernel
+// `kern` of `threads` threads (launch_shape.cu); target: the CTA count of six
+// rounds at the kernel family's design occupancy.  Cached per kernel and shape.
+int pick_zchunk(const void *kern, int threads, int tiles, int nz, int target);
 
 // How a step launch sits in the stream (programmatic dependent launch):
 //   kWaitFaces  the previous kernel refreshes src's ghosts: boxes touching a face wait for it

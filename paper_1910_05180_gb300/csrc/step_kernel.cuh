@@ -57,6 +57,13 @@ constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz per bounded w
 
 template <class T> struct Pk;
 
+// The FP32 packs run on the paired FP32 instructions.  The code generator
+// fuses a paired multiply whose result feeds a paired add into one paired FMA,
+// explicit rounding modifier or not, and decides per inlined copy; so the step
+// code never adds or subtracts a product as a separate operation: where a
+// product is summed the code writes the FMA.  Every unrolled copy of the
+// z-march then computes the same expression, and a cell gets the same bits
+// whichever CTA, z-chunk or kernel (single grid or batch) computes it.
 template <> struct Pk<float> {
     using P = float2;
     static __device__ __forceinline__ P mk(float a, float b) { return make_float2(a, b); }
@@ -81,8 +88,8 @@ struct D2 { double x, y; };
 template <> struct Pk<double> {
     using P = D2;
     static __device__ __forceinline__ P mk(double a, double b) { return {a, b}; }
-    static __device__ __forceinline__ P add(P a, P b) { return {a.x + b.x, a.y + b.y}; }
-    static __device__ __forceinline__ P mul(P a, P b) { return {a.x * b.x, a.y * b.y}; }
+    static __device__ __forceinline__ P add(P a, P b) { return {__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y)}; }
+    static __device__ __forceinline__ P mul(P a, P b) { return {__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)}; }
     static __device__ __forceinline__ P fma(P a, P b, P c)
     {
         return {__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y)};
@@ -304,49 +311,56 @@ struct TileShape {
 };
 
 // Per plane and pack: c = phi, h = c1 dt F' + c2 dt E' (the plane as the centre
-// plane of an output), g = c2 dt F' + c3 dt E' (as the plane above or below).
+// plane of an output), g = c2 dt F' + c3 dt E' (as the plane above or below);
+// with 6 neighbours h = F', with 18 g = F' (their coefficients are applied in
+// the update, by FMA).
 template <class T, int NP>
 struct PlaneQ {
     using P = typename Pk<T>::P;
     P c[NP], h[NP], g[NP];
-    P psi[NP], gx[NP], gy[NP];   // TI_n only: profile inversion and its in-plane differences
+    P psi[NP], gx[NP], gy[NP];   // TI_n only: log-odds of phi and its in-plane differences
 };
 
 // ----------------------------------------------------------------- TI_n
 
 // Inversion of the ideal profile, psi = (lambda/2) artanh(1 - 2 phi)
 // = (lambda/4) ln((1 - phi)/phi), with phi clamped to [eps, 1 - eps] (TI_n).
-__device__ __forceinline__ float psi_of(float phi, float quarter_lam, float eps)
+// The kernels keep the log-odds only (FP32 log2, FP64 ln) and scale their
+// central differences by StepCoef::psi_grad; the FP32 log-odds is the
+// hardware log2 itself, no product, so differences of equal values are 0.
+__device__ __forceinline__ float log_odds(float phi, float eps)
 {
     const float pc = fminf(fmaxf(phi, eps), 1.0f - eps);
-    return quarter_lam * __logf(__fdividef(1.0f - pc, pc));
+    return __log2f(__fdividef(1.0f - pc, pc));
 }
-__device__ __forceinline__ double psi_of(double phi, double quarter_lam, double eps)
+__device__ __forceinline__ double log_odds(double phi, double eps)
 {
     const double pc = fmin(fmax(phi, eps), 1.0 - eps);
-    return quarter_lam * log((1.0 - pc) / pc);
+    return log((1.0 - pc) / pc);
 }
 template <class T>
-__device__ __forceinline__ typename Pk<T>::P psi_pack(typename Pk<T>::P v, T quarter_lam, T eps)
+__device__ __forceinline__ typename Pk<T>::P log_odds_pack(typename Pk<T>::P v, T eps)
 {
-    return Pk<T>::mk(psi_of(v.x, quarter_lam, eps), psi_of(v.y, quarter_lam, eps));
+    return Pk<T>::mk(log_odds(v.x, eps), log_odds(v.y, eps));
 }
 // tanh of a pack.  FP32: Lambert's continued fraction for tanh truncated
 // after the term x^2/11, x (10395 + 1260 y + 21 y^2) / (10395 + 4725 y + 210 y^2 + y^3)
-// with y = x^2 (|error| < 3.3e-10 for |x| <= 1, < 3e-8 for |x| <= 1.5); callers
-// whose arguments can exceed 1.5 pass small = false and get tanhf.  FP64: tanh.
+// with y = x^2 (|error| < 3.3e-10 for |x| <= 1, < 3e-8 for |x| <= 1.5), written
+// as x - x y (3465 + 189 y + y^2) / den so that the result is an FMA and sums
+// of tanh values fuse nothing; callers whose arguments can exceed 1.5 pass
+// small = false and get tanhf.  FP64: tanh.
 template <class T> struct TanhPk;
 template <> struct TanhPk<float> {
     static __device__ __forceinline__ float2 eval(float2 x, bool small)
     {
         if (!small) return make_float2(tanhf(x.x), tanhf(x.y));
         const float2 y = __fmul2_rn(x, x);
-        const float2 num = __ffma2_rn(__ffma2_rn(y, make_float2(21.f, 21.f), make_float2(1260.f, 1260.f)), y,
-                                      make_float2(10395.f, 10395.f));
-        const float2 den = __ffma2_rn(__ffma2_rn(__fadd2_rn(y, make_float2(210.f, 210.f)), y,
+        const float2 poly = __ffma2_rn(__ffma2_rn(x, x, make_float2(189.f, 189.f)), y, make_float2(3465.f, 3465.f));
+        const float2 den = __ffma2_rn(__ffma2_rn(__ffma2_rn(x, x, make_float2(210.f, 210.f)), y,
                                                  make_float2(4725.f, 4725.f)),
                                       y, make_float2(10395.f, 10395.f));
-        return Pk<float>::div(__fmul2_rn(x, num), den);
+        const float2 r = Pk<float>::div(__fmul2_rn(y, poly), den);
+        return __ffma2_rn(r, __ffma2_rn(x, make_float2(-1.f, -1.f), make_float2(0.f, 0.f)), x);
     }
 };
 template <> struct TanhPk<double> {
@@ -439,7 +453,7 @@ __device__ __forceinline__ typename Pk<T>::P ti_local_w(const StepCoef<T> &C, ty
     // B = x'^2 + y'^2 (S and B are the squares summed over the pair), R = 2 x y
     // (= 2 x' y'), P = B - S u and v = 1 - u, the pair's two terms
     // n/d = (S +- R) / (P +- R v) add up to 2 (S P - R^2 v) / (P^2 - R^2 v^2).
-    const P v = K::add(one, neg_u);
+    const P v = K::fma(K::sub(zero, sg), sg, one);   // 1 - s^2
     const P m4 = K::mk(T(-4), T(-4));
     auto pair = [&](P &pn, P &pd, P S, P B, P r) {   // r = x^2 y^2 = R^2 / 4
         const P Pv = K::fma(S, neg_u, B);
@@ -450,9 +464,9 @@ __device__ __forceinline__ typename Pk<T>::P ti_local_w(const StepCoef<T> &C, ty
         // shell 2: (1,+-1,0), (0,1,+-1), (1,0,+-1): x, y = t_i, t_j and x', y' = t_i t_j, 1
         P n2 = zero, d2 = one;
         const P ab = K::mul(a2, b2), bc = K::mul(b2, c2), ac = K::mul(a2, c2);
-        pair(n2, d2, K::add(a2, b2), K::add(one, ab), ab);
-        pair(n2, d2, K::add(b2, c2), K::add(one, bc), bc);
-        pair(n2, d2, K::add(a2, c2), K::add(one, ac), ac);
+        pair(n2, d2, K::fma(a, a, b2), K::fma(a2, b2, one), ab);
+        pair(n2, d2, K::fma(b, b, c2), K::fma(b2, c2, one), bc);
+        pair(n2, d2, K::fma(a, a, c2), K::fma(a2, c2, one), ac);
         acc(num, den, K::mul(K::mk(T(-8) * C.dt * C.ck[3], T(-8) * C.dt * C.ck[3]), n2), d2);
     }
     if (STENCIL >= 26 && C.ck[9] != T(0)) {
@@ -460,9 +474,8 @@ __device__ __forceinline__ typename Pk<T>::P ti_local_w(const StepCoef<T> &C, ty
         // (1,1,+-1): N = al +- tz be, D = be +- tz al with al = tx + ty, be = 1 + tx ty;
         // (-1,1,1), (1,-1,1): the same with al = ty - tx, be = 1 - tx ty.
         P n3 = zero, d3 = one;
-        const P ab = K::mul(a, b);
-        const P al1 = K::add(a, b), be1 = K::add(one, ab);
-        const P al2 = K::sub(b, a), be2 = K::sub(one, ab);
+        const P al1 = K::add(a, b), be1 = K::fma(a, b, one);
+        const P al2 = K::sub(b, a), be2 = K::fma(K::sub(zero, a), b, one);
         const P A1 = K::mul(al1, al1), B1 = K::mul(be1, be1);
         const P A2 = K::mul(al2, al2), B2 = K::mul(be2, be2);
         pair(n3, d3, K::fma(c2, B1, A1), K::fma(c2, A1, B1), K::mul(K::mul(A1, B1), c2));
@@ -583,6 +596,23 @@ __device__ __forceinline__ void fix_z(S *dst, const S *src, const GridGeom &g, c
 {
     const FaceMap<T> m = face_map<T>(g.bc[face], aface[face]);
     for (int i = lane; i < ROWS * SW; i += 32) dst[i] = Io<S, T>::cvt_out(face_value(Io<S, T>::cvt_in(src[i]), m));
+}
+
+// phi + dt (Laplacian part of Eq. 1) of a pack from its plane records: t the
+// z-neighbour differences, h of the centre plane, g of the planes below and
+// above (6 neighbours: h = F'; 18: g = F'; 26: h, g with their coefficients).
+// SR: the increment alone (phi is added in sr_update).  Products are summed by
+// FMAs only.
+template <bool SR, int STENCIL, class P, class PCoef>
+__device__ __forceinline__ P laplace_update(const PCoef &PC, P t, P ph, P h, P gm, P gp)
+{
+    using K = Pk<decltype(P().x)>;
+    P acc;
+    if constexpr (STENCIL == 6) acc = K::fma(PC.c1, h, SR ? K::mul(PC.ct, t) : K::fma(PC.ct, t, ph));
+    else acc = SR ? K::fma(PC.ct, t, h) : K::add(K::fma(PC.ct, t, ph), h);
+    if constexpr (STENCIL == 18) acc = K::fma(PC.c2, K::add(gm, gp), acc);
+    if constexpr (STENCIL == 26) acc = K::add(acc, K::add(gm, gp));
+    return acc;
 }
 
 // KIND: 0 = CF potential; 1..4 = TI global with exactly KIND coupling groups;
@@ -766,29 +796,31 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
                     // F' = (W + E + N + S) - 4C, E' = (NW + NE + SW + SE) - 4C
                     const P f = K::fma(PC.m4, c, K::add(K::add(rw[r + 1][q], re[r + 1][q]),
                                                         K::add(rc[r][q], rc[r + 2][q])));
+                    // 6 neighbours: h = F' (c1 applied in the update's FMA); 18: g = F'
+                    // (c2 applied to the sum of the two planes' g in one FMA)
                     if (STENCIL == 6) {
-                        p[r].h[q] = K::mul(PC.c1, f);
+                        p[r].h[q] = f;
                     } else {
                         const P e = K::fma(PC.m4, c, K::add(K::add(rw[r][q], re[r][q]),
                                                             K::add(rw[r + 2][q], re[r + 2][q])));
                         p[r].h[q] = K::fma(PC.c2, e, K::mul(PC.c1, f));
-                        p[r].g[q] = STENCIL == 26 ? K::fma(PC.c3, e, K::mul(PC.c2, f)) : K::mul(PC.c2, f);
+                        p[r].g[q] = STENCIL == 26 ? K::fma(PC.c3, e, K::mul(PC.c2, f)) : f;
                     }
                 }
                 if (KIND == 6) {
-                    // psi at the cells and central differences along x and y.  A
+                    // log-odds at the cells and central differences along x and y.  A
                     // warp holds 32/TX rows: each lane inverts its own cells and
                     // its row's two x-neighbour cells; the rows above and below
                     // come by shuffle from the lanes TX away, except beyond the
                     // warp's first and last rows, where the lane inverts them.
                     static_assert(KIND != 6 || (TX <= 16 && 32 % TX == 0), "TI_n needs two or more rows a warp");
-                    const T ql = C.half_lam * T(0.5), ep = C.eps;
+                    const T ep = C.eps;
                     const bool first = lane < TX, last = lane >= 32 - TX;
                     T own[VX], outer[VX];
 #pragma unroll
                     for (int q = 0; q < NP; ++q) {
-                        const P po = psi_pack<T>(rc[r + 1][q], ql, ep);
-                        const P pb = psi_pack<T>(first ? rc[r][q] : rc[r + 2][q], ql, ep);
+                        const P po = log_odds_pack<T>(rc[r + 1][q], ep);
+                        const P pb = log_odds_pack<T>(first ? rc[r][q] : rc[r + 2][q], ep);
                         p[r].psi[q] = po;
                         own[2 * q] = po.x;
                         own[2 * q + 1] = po.y;
@@ -796,18 +828,17 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
                         outer[2 * q + 1] = pb.y;
                     }
                     // the two x-neighbour cells of the thread's run
-                    const P pwe = psi_pack<T>(K::mk(rw[r + 1][0].x, re[r + 1][NP - 1].y), ql, ep);
+                    const P pwe = log_odds_pack<T>(K::mk(rw[r + 1][0].x, re[r + 1][NP - 1].y), ep);
                     const T pw = pwe.x;   // x - 1
                     const T pe = pwe.y;   // x + VX
 #pragma unroll
                     for (int q = 0; q < NP; ++q) {
                         const T w0 = 2 * q == 0 ? pw : own[2 * q - 1];
                         const T e1 = 2 * q + 2 == VX ? pe : own[2 * q + 2];
-                        // K::sub is an explicit fused op that the compiler cannot merge
-                        // with the multiply inside psi: equal psi then differ by exactly
-                        // zero, and a clamped region keeps the CF fallback (a contracted
-                        // difference leaves the rounding error of that multiply, enough
-                        // to pass |g| >= 1e-8 in FP32 with a meaningless normal)
+                        // the log-odds are no products, so equal values differ by exactly
+                        // zero and a clamped region keeps the CF fallback (a difference
+                        // fused with a multiply would leave that product's rounding
+                        // error, enough to pass |g| >= 1e-8 in FP32 with a meaningless normal)
                         p[r].gx[q] = K::sub(K::mk(own[2 * q + 1], e1), K::mk(w0, own[2 * q]));
                         T nb[2], sb[2];
 #pragma unroll
@@ -842,9 +873,7 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
                         const P ph = z[r].c[q];
                         const P t = K::add(K::sub(m[r].c[q], ph), K::sub(p[r].c[q], ph));
                         // SR: the increment alone, phi is added once in sr_update
-                        if constexpr (SR) acc[q] = K::fma(PC.ct, t, z[r].h[q]);
-                        else acc[q] = K::add(K::fma(PC.ct, t, ph), z[r].h[q]);
-                        if (STENCIL != 6) acc[q] = K::add(acc[q], K::add(m[r].g[q], p[r].g[q]));
+                        acc[q] = laplace_update<SR, STENCIL>(PC, t, ph, z[r].h[q], m[r].g[q], p[r].g[q]);
                         sg[q] = K::fma(PC.m2, ph, PC.one);
                         q1[q] = K::mul(ph, K::sub(PC.one, ph));
                         u[q] = K::mul(sg[q], sg[q]);
@@ -876,10 +905,7 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
                         const P ph = z[r].c[q];
                         const P t = K::add(K::sub(m[r].c[q], ph), K::sub(p[r].c[q], ph));
                         // phi + dt * Laplacian (SR: the increment alone, phi is added in sr_update)
-                        P acc;
-                        if constexpr (SR) acc = K::fma(PC.ct, t, z[r].h[q]);
-                        else acc = K::add(K::fma(PC.ct, t, ph), z[r].h[q]);
-                        if (STENCIL != 6) acc = K::add(acc, K::add(m[r].g[q], p[r].g[q]));
+                        const P acc = laplace_update<SR, STENCIL>(PC, t, ph, z[r].h[q], m[r].g[q], p[r].g[q]);
                         const P sg = K::fma(PC.m2, ph, PC.one);               // s = 1 - 2 phi
                         const P q1 = K::mul(ph, K::sub(PC.one, ph));          // q = phi (1 - phi)
                         P w;   // -dt (potential / q + 4 M dF / (lambda Gamma))
@@ -895,7 +921,7 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
                             }
                             w = K::fma(sg, PC.nkap, drive);
                         } else if (KIND == 6) {
-                            const P s2 = K::mk(C.inv_2dx, C.inv_2dx);
+                            const P s2 = K::mk(C.psi_grad, C.psi_grad);
                             const P gz = K::mul(K::sub(p[r].psi[q], m[r].psi[q]), s2);
                             w = ti_local_w<T, STENCIL>(C, sg, K::mul(sg, sg), K::mul(z[r].gx[q], s2),
                                                        K::mul(z[r].gy[q], s2), gz);
@@ -1115,17 +1141,6 @@ cudaError_t launch_batch_t(const void *grids, const BatchItem *work, int nwork, 
     return cudaGetLastError();
 }
 
-// z-chunk length so that the launch has about `target` CTAs (chunks of 16
-// planes or more)
-inline int pick_zchunk(int tiles_xy, int nz, int target)
-{
-    int chunks = (target + tiles_xy - 1) / tiles_xy;
-    int max_chunks = nz / 16 > 1 ? nz / 16 : 1;
-    if (chunks > max_chunks) chunks = max_chunks;
-    if (chunks < 1) chunks = 1;
-    return (nz + chunks - 1) / chunks;
-}
-
 // IMG: the kernels that write the periodic ghost images (cfg.mode has kImages)
 template <class S, class T, int TX, int TY, bool IMG, bool SR = false>
 cudaError_t launch_step_t(const StepCoef<T> &c, const S *src, S *dst, int *err, LaunchCfg cfg,
@@ -1133,13 +1148,10 @@ cudaError_t launch_step_t(const StepCoef<T> &c, const S *src, S *dst, int *err, 
 {
     using Sh = TileShape<S, T, TX, TY>;
     const int gxn = (c.g.nx + Sh::W - 1) / Sh::W, gyn = (c.g.ny + TY - 1) / TY;
-    // about six waves of the resident CTAs: fewer, longer CTAs leave a longer
-    // tail, shorter ones re-read more halo planes (512^3 FP32 sweep)
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int zchunk = pick_zchunk(gxn * gyn, c.g.nz, 6 * MinBlocks<S>::value * sms);
-    const dim3 grid(gxn, gyn, (c.g.nz + zchunk - 1) / zchunk);
+    const int target = 6 * MinBlocks<S>::value * sms;
     // exact group counts 1..4 get their own kernels; 0 groups (all A_k = 0)
     // runs the one-group kernel with beta = 0
     const int kind = is_fd_scheme(cfg.scheme) ? 0
@@ -1158,13 +1170,19 @@ cudaError_t launch_step_t(const StepCoef<T> &c, const S *src, S *dst, int *err, 
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cudaLaunchConfig_t lc = {};
-    lc.gridDim = grid;
     lc.dynamicSmemBytes = 0;
     lc.stream = st;
     lc.attrs = attr;
     lc.numAttrs = 1;
     const int mode = cfg.mode;
+    // z-chunk: the caller's, else the launch-shape model's for this kernel (a
+    // grid dimension stays below 65536 chunks)
     auto go = [&](auto kern, int threads) {
+        int zchunk = cfg.zchunk > 0 ? cfg.zchunk : pick_zchunk((const void *)kern, threads, gxn * gyn, c.g.nz, target);
+        if (zchunk > c.g.nz) zchunk = c.g.nz;
+        if (zchunk < (c.g.nz + 65534) / 65535) zchunk = (c.g.nz + 65534) / 65535;
+        if (cfg.zchunk_used) *cfg.zchunk_used = zchunk;
+        lc.gridDim = dim3(gxn, gyn, (c.g.nz + zchunk - 1) / zchunk);
         lc.blockDim = dim3(threads);
         return cudaLaunchKernelEx(&lc, kern, c, pc, src, dst, err, zchunk, map, use, mode);
     };

@@ -95,6 +95,8 @@ SIGNATURES = [
     ("spfm_step_conserving", _I, [_P, _I, _D, _D, _D, _D, _D, _I, _I, ctypes.POINTER(_D)]),
     ("spfm_set_rounding", _I, [_P, _I, ctypes.c_ulonglong]),
     ("spfm_debug_skip_copy", _I, [_P]),
+    ("spfm_set_zchunk", _I, [_P, _I]),
+    ("spfm_last_zchunk", _I, [_P]),
     ("spfm_shift_x", _I, [_P, _I]),
     ("spfm_max_dt", _I, [_P, _D, _D, _D, _D, _D, _I, _I, ctypes.POINTER(_D)]),
     ("spfm_interface_stats", _I, [_P, _I, ctypes.POINTER(Stats)]),
@@ -171,6 +173,10 @@ def spfm_set_rounding(h, mode, seed=0):
 
 def spfm_debug_skip_copy(h):
     _check(load().spfm_debug_skip_copy(h), h)
+
+
+def spfm_set_zchunk(h, zchunk):
+    _check(load().spfm_set_zchunk(h, int(zchunk)), h)
 
 
 def spfm_init_planar(h, c, lam, dx):
@@ -315,6 +321,14 @@ class Grid:
     def set_rounding(self, mode, seed=0):
         """SPFM_ROUND_NEAREST or SPFM_ROUND_STOCHASTIC (FP32/BF16) for the following steps."""
         spfm_set_rounding(self.handle, mode, seed)
+
+    def set_zchunk(self, zchunk):
+        """Planes per CTA of the step launches (0: chosen per launch); the field is the same for any."""
+        spfm_set_zchunk(self.handle, zchunk)
+
+    def last_zchunk(self):
+        """Planes per CTA of the last step launch (0 before the first step)."""
+        return int(load().spfm_last_zchunk(self.handle))
 
     def shift_x(self, cells):
         """Moving frame: phi_i <- phi_{i+cells} (end cells repeated)."""

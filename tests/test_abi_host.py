@@ -203,6 +203,19 @@ def test_rounding_mode_validation(lib):
     assert lib.spfm_set_rounding(None, S.SPFM_ROUND_NEAREST, 0) == S.SPFM_EINVAL
 
 
+def test_zchunk_validation(lib):
+    """The z-chunk knob takes 0 (per launch) or any positive plane count."""
+    h = _fake_grid(lib)
+    assert lib.spfm_last_zchunk(h) == 0          # no step launched yet
+    for zc in (0, 1, 7, 10 ** 6):
+        assert lib.spfm_set_zchunk(h, zc) == S.SPFM_OK
+    assert lib.spfm_set_zchunk(h, -1) == S.SPFM_EINVAL
+    assert b"zchunk" in lib.spfm_last_error(h)
+    lib.spfm_destroy_grid(h)
+    assert lib.spfm_set_zchunk(None, 0) == S.SPFM_EINVAL
+    assert lib.spfm_last_zchunk(None) == -1
+
+
 def test_last_error_is_thread_local_without_grid(lib):
     with pytest.raises(S.SpfmError):
         S.spfm_layout(_desc(dtype=9))

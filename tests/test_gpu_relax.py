@@ -34,12 +34,15 @@ def test_init_cube_matches_oracle(dtype):
     assert np.abs(g.get_field(to_host=True).double().numpy() - ref).max() <= tol
 
 
-@pytest.mark.parametrize("dtype", [S.SPFM_F64, S.SPFM_F32])
+@pytest.mark.parametrize("dtype,rounding", [(S.SPFM_F64, S.SPFM_ROUND_NEAREST), (S.SPFM_F32, S.SPFM_ROUND_NEAREST),
+                                            (S.SPFM_F32, S.SPFM_ROUND_STOCHASTIC)])
 @pytest.mark.parametrize("scheme,oscheme", SCHEMES)
-def test_conserving_steps_match_oracle(dtype, scheme, oscheme):
+def test_conserving_steps_match_oracle(dtype, rounding, scheme, oscheme):
+    """Stochastic rounding applies to the step before the correction."""
     N, lam, dt, steps = 32, 2.5, 0.05, 40
     ctr = ((N - 1) / 2.0,) * 3
     g = S.Grid(N, N, N, dtype=dtype, bc=(S.SPFM_PERIODIC,) * 6, n=U120)
+    g.set_rounding(rounding, seed=3)
     p = O.Params(N, N, N, bc=(O.PERIODIC,) * 6, n=U120, lam=lam, dt=dt, stencil=26, scheme=oscheme)
     g.init_cube(ctr, 8.0, lam)
     start = g.get_field(to_host=True).double().numpy()

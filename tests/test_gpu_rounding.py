@@ -180,3 +180,20 @@ def test_batch_refuses_mixed_rounding():
         b.step(1, [S.step_args(lam=3.0, dt=0.05, stencil=26)] * 2)
     assert e.value.status == S.SPFM_EINVAL and "rounding" in str(e.value)
     b.close()
+
+
+def test_conserving_steps_take_the_rounding_mode():
+    """Constant-volume steps round their step as the grid's mode says: the same
+    seed gives the same field, round to nearest another one."""
+    N, lam = 32, 2.5
+    ctr = ((N - 1) / 2.0,) * 3
+    out = []
+    for mode, seed in ((S.SPFM_ROUND_STOCHASTIC, 4), (S.SPFM_ROUND_STOCHASTIC, 4), (S.SPFM_ROUND_NEAREST, 4)):
+        g = S.Grid(N, N, N, dtype=S.SPFM_F32, bc=(S.SPFM_PERIODIC,) * 6, n=tuple(UNIT([1.0, 2.0, 0.0])))
+        g.set_rounding(mode, seed=seed)
+        g.init_cube(ctr, 8.0, lam)
+        g.step_conserving(20, lam=lam, dt=0.05, stencil=26)
+        out.append(g.get_field())
+        g.close()
+    assert torch.equal(out[0], out[1])
+    assert not torch.equal(out[0], out[2])
