@@ -285,6 +285,12 @@ __host__ __device__ __forceinline__ DF df_of(double x)
     return {h, (float)(x - (double)h)};
 }
 __device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
+// an integer index as an exact pair (|n| < 2^48)
+__device__ __forceinline__ DF df_of_int(int n)
+{
+    const float h = (float)n;
+    return {h, (float)(n - (int)h)};
+}
 // sqrt of a non-negative value: the FP32 root s and one Newton step,
 // s + (a - s^2) / (2 s), with s^2 formed exactly
 __device__ __forceinline__ DF df_sqrt(DF a)
@@ -293,7 +299,8 @@ __device__ __forceinline__ DF df_sqrt(DF a)
     const float s = sqrtf(a.hi);
     const DF s2 = df_two_prod(s, s);
     const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, s2.hi), s2.lo), a.lo);
-    return df_fast_sum(s, __fmul_rn(r, __fdiv_rn(0.5f, s)));
+    // the correction is about 2^-24 of s: an approximate reciprocal keeps the pair's accuracy
+    return df_fast_sum(s, __fmul_rn(r, __fdividef(0.5f, s)));
 }
 
 // Tables of the band evaluation, as double-float pairs written from FP64:
@@ -354,7 +361,7 @@ template <class R> struct BandCell {
 // psi = (lambda/2) artanh(1 - 2 phi) = (lambda/4) (ln(1 - phi) - ln phi),
 // p = dx (i, j, k).  Absolute error of psi below about 1e-13.
 struct BandConst {
-    DF dxn0, dx, neg_c0, quarter_lambda;
+    DF dxn0, dxn1, dxn2, dx, neg_c0, neg_c1, neg_c2, quarter_lambda;
 };
 template <class R> struct BandPhi;
 template <> struct BandPhi<float> {   // FP32 and BF16 storage: phi exact, 1 - phi exact as a pair
@@ -386,9 +393,9 @@ __device__ __forceinline__ void band_cell(const BandConst &bc, const BandCell<R>
     DF d = df_add(DF{kl.x, kl.y}, df_add(l1.lnF, df_neg(l0.lnF)));
     d = df_add(d, df_add(l1.s, df_neg(l0.s)));
     const DF psi = df_mul(bc.quarter_lambda, d);
-    const float fi = (float)c.i;
-    const DF pn = df_add(c.pn_row, df_mul_f(bc.dxn0, fi));
-    const DF rx = df_add(df_mul_f(bc.dx, fi), bc.neg_c0);
+    const DF fi = df_of_int(c.i);
+    const DF pn = df_add(c.pn_row, df_mul(bc.dxn0, fi));
+    const DF rx = df_add(df_mul(bc.dx, fi), bc.neg_c0);
     const DF r = df_sqrt(df_add(df_mul(rx, rx), c.ryz2));
     acc.w = df_add_acc(acc.w, q);
     acc.c = df_add_acc(acc.c, df_mul(q, df_add(pn, df_neg(psi))));
@@ -416,13 +423,19 @@ __device__ __forceinline__ void stats_pass(const StatsArgs &a, const S *f, doubl
     for (int i = 0; i < kNStat; ++i) v[i] = 0.0;
     R mn = R(INFINITY), mx = R(-INFINITY);
     int nonfinite = 0, cnt = 0;
-    const BandConst bconst = {df_of(a.dx * a.n[0]), df_of(a.dx), df_of(-a.ctr[0]), df_of(0.25 * a.lambda)};
+    const BandConst bconst = {df_of(a.dx * a.n[0]), df_of(a.dx * a.n[1]), df_of(a.dx * a.n[2]), df_of(a.dx),
+                              df_of(-a.ctr[0]),      df_of(-a.ctr[1]),      df_of(-a.ctr[2]), df_of(0.25 * a.lambda)};
     BandSums sums;
     VolSum<R> vol;
     const long long rows = (long long)a.g.ny * a.g.nz;
     const int nvec = (a.g.nx + E - 1) / E;
-    for (long long row = blk * kWarps + warp; row < rows; row += nblk * kWarps) {
-        const int j = (int)(row % a.g.ny), k = (int)(row / a.g.ny);
+    // rows (j, k) dealt round-robin to the warps; ny nz < 2^30, and (j, k)
+    // advance by the stride's split so that no row divides (64-bit division
+    // is emulated in FP64, the slow pipe of this GPU)
+    const long long row0 = blk * kWarps + warp, stride = nblk * kWarps;
+    const int sj = (int)(stride % a.g.ny), sk = (int)(stride / a.g.ny);
+    for (int j = (int)(row0 % a.g.ny), k = (int)(row0 / a.g.ny); k < a.g.nz;
+         j += sj, k += sk, (j >= a.g.ny ? (j -= a.g.ny, ++k) : 0)) {
         DF pn_row{0.0f, 0.0f}, ryz2{0.0f, 0.0f};   // the row's shares, once it has band cells
         bool row_known = false;
         const uint4 *src = (const uint4 *)(f + cell_index(a.g, 0, j, k));
@@ -452,11 +465,13 @@ __device__ __forceinline__ void stats_pass(const StatsArgs &a, const S *f, doubl
                     }
                 }
             // queue this sweep's band cells, evaluating full warps of them
+            // the row's shares in double-float (FP64 is the slow pipe of this GPU)
             if (!row_known && __any_sync(0xffffffffu, bm != 0u)) {
-                const double py = a.dx * j, pz = a.dx * k;
-                pn_row = df_of(py * a.n[1] + pz * a.n[2]);
-                const double ry = py - a.ctr[1], rz = pz - a.ctr[2];
-                ryz2 = df_of(ry * ry + rz * rz);
+                const DF fj = df_of_int(j), fk = df_of_int(k);
+                pn_row = df_add(df_mul(bconst.dxn1, fj), df_mul(bconst.dxn2, fk));
+                const DF ry = df_add(df_mul(bconst.dx, fj), bconst.neg_c1);
+                const DF rz = df_add(df_mul(bconst.dx, fk), bconst.neg_c2);
+                ryz2 = df_add(df_mul(ry, ry), df_mul(rz, rz));
                 row_known = true;
             }
             while (__any_sync(0xffffffffu, bm != 0u)) {
