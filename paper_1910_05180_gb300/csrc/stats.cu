@@ -413,19 +413,39 @@ __device__ __forceinline__ void stats_pass(const StatsArgs &a, const S *f, doubl
     constexpr int E = Row16<S>::E;        // elements per 16-byte load
     constexpr int V = 16 / E;             // loads per lane and sweep
     constexpr int kWarps = 8;
-    __shared__ BandCell<R> queue[kWarps][64];
+    // Per warp: a ring of band cells (value, x index) with the slot of their
+    // row's shares; a sweep is queued in four parts of at most 128 cells and
+    // full warps of 32 are evaluated after each, so fewer than 32 wait between
+    // parts and a part always fits.  Waiting cells come from fewer than 32 rows,
+    // so 32 row slots, taken in turn, are never overwritten while referenced.
+    constexpr int kRing = 256, kRowSlots = 32;
+    __shared__ R ring_phi[kWarps][kRing];
+    __shared__ int ring_i[kWarps][kRing];
+    __shared__ unsigned char ring_slot[kWarps][kRing];
+    __shared__ DF row_tab[kWarps][kRowSlots][2];
     const float4 *tab = g_ln_tab;
     const float2 *kln2 = g_kln2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    BandCell<R> *qw = queue[warp];
     double v[kNStat];
 #pragma unroll
     for (int i = 0; i < kNStat; ++i) v[i] = 0.0;
     R mn = R(INFINITY), mx = R(-INFINITY);
-    int nonfinite = 0, cnt = 0;
+    int nonfinite = 0;
     const BandConst bconst = {df_of(a.dx * a.n[0]), df_of(a.dx * a.n[1]), df_of(a.dx * a.n[2]), df_of(a.dx),
                               df_of(-a.ctr[0]),      df_of(-a.ctr[1]),      df_of(-a.ctr[2]), df_of(0.25 * a.lambda)};
     BandSums sums;
+    int head = 0, tail = 0, band_rows = 0;   // ring positions and band rows so far (warp-uniform)
+    // evaluate the waiting cell at ring position q (this lane's)
+    auto eval_at = [&](int q) {
+        const int r = q & (kRing - 1);
+        BandCell<R> c;
+        c.phi = ring_phi[warp][r];
+        c.i = ring_i[warp][r];
+        const int sl = ring_slot[warp][r];
+        c.pn_row = row_tab[warp][sl][0];
+        c.ryz2 = row_tab[warp][sl][1];
+        band_cell<R>(bconst, c, tab, kln2, sums);
+    };
     VolSum<R> vol;
     const long long rows = (long long)a.g.ny * a.g.nz;
     const int nvec = (a.g.nx + E - 1) / E;
@@ -436,8 +456,8 @@ __device__ __forceinline__ void stats_pass(const StatsArgs &a, const S *f, doubl
     const int sj = (int)(stride % a.g.ny), sk = (int)(stride / a.g.ny);
     for (int j = (int)(row0 % a.g.ny), k = (int)(row0 / a.g.ny); k < a.g.nz;
          j += sj, k += sk, (j >= a.g.ny ? (j -= a.g.ny, ++k) : 0)) {
-        DF pn_row{0.0f, 0.0f}, ryz2{0.0f, 0.0f};   // the row's shares, once it has band cells
-        bool row_known = false;
+        bool row_known = false;   // the row's shares are in its slot
+        int slot = 0;
         const uint4 *src = (const uint4 *)(f + cell_index(a.g, 0, j, k));
         for (int v0 = 0; v0 < nvec; v0 += 32 * V) {
             uint4 w[V];
@@ -464,46 +484,56 @@ __device__ __forceinline__ void stats_pass(const StatsArgs &a, const S *f, doubl
                         }
                     }
                 }
-            // queue this sweep's band cells, evaluating full warps of them
-            // the row's shares in double-float (FP64 is the slow pipe of this GPU)
-            if (!row_known && __any_sync(0xffffffffu, bm != 0u)) {
-                const DF fj = df_of_int(j), fk = df_of_int(k);
-                pn_row = df_add(df_mul(bconst.dxn1, fj), df_mul(bconst.dxn2, fk));
-                const DF ry = df_add(df_mul(bconst.dx, fj), bconst.neg_c1);
-                const DF rz = df_add(df_mul(bconst.dx, fk), bconst.neg_c2);
-                ryz2 = df_add(df_mul(ry, ry), df_mul(rz, rz));
-                row_known = true;
-            }
-            while (__any_sync(0xffffffffu, bm != 0u)) {
-                const int b = bm ? __ffs(bm) - 1 : -1;
-                bm &= bm - 1u;
-                R x = R(0);
-#pragma unroll
-                for (int u = 0; u < E * V; ++u) x = b == u ? Row16<S>::get(w[u / E], u % E) : x;
-                const unsigned m = __ballot_sync(0xffffffffu, b >= 0);
-                if (b >= 0) {
-                    BandCell<R> &c = qw[cnt + __popc(m & ((1u << lane) - 1u))];
-                    c.phi = x;
-                    c.i = (v0 + 32 * (b / E) + lane) * E + b % E;
-                    c.pn_row = pn_row;
-                    c.ryz2 = ryz2;
+            if (__any_sync(0xffffffffu, bm != 0u)) {
+                if (!row_known) {
+                    // the row's shares of p.n and |p - ctr|^2, in double-float (FP64
+                    // is the slow pipe of this GPU)
+                    slot = band_rows++ & (kRowSlots - 1);
+                    if (lane == 0) {
+                        const DF fj = df_of_int(j), fk = df_of_int(k);
+                        const DF ry = df_add(df_mul(bconst.dx, fj), bconst.neg_c1);
+                        const DF rz = df_add(df_mul(bconst.dx, fk), bconst.neg_c2);
+                        row_tab[warp][slot][0] = df_add(df_mul(bconst.dxn1, fj), df_mul(bconst.dxn2, fk));
+                        row_tab[warp][slot][1] = df_add(df_mul(ry, ry), df_mul(rz, rz));
+                    }
+                    row_known = true;
                 }
-                cnt += __popc(m);
-                if (cnt >= 32) {
+                // queue the sweep's band cells in four parts (a warp prefix sum
+                // places each lane's cells), evaluating full warps after each
+#pragma unroll
+                for (int part = 0; part < 4; ++part) {
+                    const unsigned m = (bm >> (4 * part)) & 0xfu;
+                    const int c = __popc(m);
+                    int incl = c;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+                        if (lane >= d) incl += y;
+                    }
+                    int pos = tail + incl - c;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        constexpr int kE = E;
+                        const int b = 4 * part + u;
+                        if (m & (1u << u)) {
+                            const int r = pos & (kRing - 1);
+                            ring_phi[warp][r] = Row16<S>::get(w[b / kE], b % kE);
+                            ring_i[warp][r] = (v0 + 32 * (b / kE) + lane) * kE + b % kE;
+                            ring_slot[warp][r] = (unsigned char)slot;
+                            ++pos;
+                        }
+                    }
+                    tail += __shfl_sync(0xffffffffu, incl, 31);
                     __syncwarp();
-                    band_cell<R>(bconst, qw[lane], tab, kln2, sums);
-                    __syncwarp();
-                    cnt -= 32;
-                    if (lane < cnt) qw[lane] = qw[lane + 32];
-                    __syncwarp();
+                    for (; tail - head >= 32; head += 32) eval_at(head + lane);
+                    __syncwarp();   // reads of evaluated cells before the next part's writes
                 }
             }
         }
         vol.end_row();
     }
     v[0] = vol.total();
-    __syncwarp();
-    if (lane < cnt) band_cell<R>(bconst, qw[lane], tab, kln2, sums);
+    if (lane < tail - head) eval_at(head + lane);
     v[1] = df_to_double(sums.w);
     v[2] = df_to_double(sums.c);
     v[3] = df_to_double(sums.r);
