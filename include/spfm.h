@@ -153,6 +153,12 @@ spfm_status spfm_set_zchunk(spfm_grid *g, int zchunk);
  * -1 for a NULL grid). */
 int spfm_last_zchunk(const spfm_grid *g);
 
+/* Test hook (the paper has no counterpart): the chunk length the automatic
+ * choice gives a launch of `tiles` xy tiles over nz planes, for a kernel of
+ * per_sm resident CTAs per SM on sms SMs, with `target` CTAs for grids of many
+ * rounds.  Host only, no device call.  -1 for an argument below 1. */
+int spfm_debug_pick_zchunk(int tiles, int nz, int per_sm, int sms, int target);
+
 /* Test hook of the failure reporting (the paper has no counterpart): the next
  * spfm_step launch skips the copy of one plane in its first CTA, whose bounded
  * waits (about 2 s each) then give up; the kernel returns without writing that

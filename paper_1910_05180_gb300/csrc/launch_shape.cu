@@ -124,3 +124,9 @@ int pick_zchunk(const void *kern, int threads, int tiles, int nz, int target)
 }
 
 }  // namespace spfm
+
+extern "C" int spfm_debug_pick_zchunk(int tiles, int nz, int per_sm, int sms, int target)
+{
+    if (tiles < 1 || nz < 1 || per_sm < 1 || sms < 1 || target < 1) return -1;
+    return spfm::model_zchunk(tiles, nz, per_sm, per_sm * sms, target);
+}

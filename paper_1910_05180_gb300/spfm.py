@@ -97,6 +97,7 @@ SIGNATURES = [
     ("spfm_debug_skip_copy", _I, [_P]),
     ("spfm_set_zchunk", _I, [_P, _I]),
     ("spfm_last_zchunk", _I, [_P]),
+    ("spfm_debug_pick_zchunk", _I, [_I, _I, _I, _I, _I]),
     ("spfm_shift_x", _I, [_P, _I]),
     ("spfm_max_dt", _I, [_P, _D, _D, _D, _D, _D, _I, _I, ctypes.POINTER(_D)]),
     ("spfm_interface_stats", _I, [_P, _I, ctypes.POINTER(Stats)]),

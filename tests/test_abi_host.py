@@ -4,8 +4,10 @@ arguments before any CUDA call (validation runs first in every entry point).
 """
 import ctypes
 import glob
+import heapq
 import math
 import os
+import random
 import re
 
 import numpy as np
@@ -214,6 +216,63 @@ def test_zchunk_validation(lib):
     lib.spfm_destroy_grid(h)
     assert lib.spfm_set_zchunk(None, 0) == S.SPFM_EINVAL
     assert lib.spfm_last_zchunk(None) == -1
+
+
+def _dispatch_makespan(tiles, nz, zc, slots, h=1, w=2):
+    """Greedy dispatch, CTA by CTA in launch order (z-chunks outermost), of the
+    launch's CTAs to `slots` slots: a CTA takes its planes + h units, w more
+    when it had to wait for a slot."""
+    free = [0] * slots
+    end, n = 0, 0
+    for c in range(-(-nz // zc)):
+        d = min(zc, nz - c * zc) + h
+        for _ in range(tiles):
+            t = heapq.heappop(free) + (w if n >= slots else 0)
+            heapq.heappush(free, t + d)
+            end, n = max(end, t + d), n + 1
+    return end
+
+
+def test_zchunk_model_is_the_dispatch_argmin(lib):
+    """For launches of few rounds the chunk length is the one of 4..64 planes
+    whose greedy dispatch ends first (ties to the longer chunk), checked against
+    a CTA-by-CTA simulation; launches of many rounds, and kernels with fewer
+    than three CTAs per SM, take about `target` CTAs in chunks of 16 planes or
+    more."""
+    rng = random.Random(3)
+    for _ in range(40):
+        tiles, nz = rng.randint(1, 40), rng.randint(5, 120)
+        per_sm, sms = rng.choice([3, 4]), rng.choice([2, 5, 9])
+        slots, target = per_sm * sms, 6 * 4 * sms
+        got = lib.spfm_debug_pick_zchunk(tiles, nz, per_sm, sms, target)
+        if tiles * -(-nz // 16) >= 4 * slots:
+            chunks = max(1, min(-(-target // tiles), max(1, nz // 16)))
+            assert got == -(-nz // chunks)
+        else:
+            spans = {z: _dispatch_makespan(tiles, nz, z, slots) for z in range(4, min(nz, 64) + 1)}
+            best = min(spans.values())
+            assert got == max(z for z, v in spans.items() if v == best), (tiles, nz, slots, got)
+
+
+@pytest.mark.parametrize("tiles,nz,per_sm,want", [
+    (16, 128, 4, 4),      # 128^3 FP32 (64 x 16 tiles): 32 chunks fill one round
+    (30, 160, 4, 8),
+    (36, 192, 4, 12),
+    (56, 224, 4, 22),
+    (64, 256, 4, 28),     # 256^3 tilted plane: 576 CTAs + 64 of 4 planes
+    (256, 512, 4, 35),    # 512^3: many rounds, 3840 CTAs of 35 planes
+    (64, 256, 2, 16),     # TI_n (two CTAs per SM): the rule of many rounds
+    (64, 3, 4, 3),        # a grid of at most 4 planes is one chunk
+])
+def test_zchunk_model_picks_measured_lengths(lib, tiles, nz, per_sm, want):
+    """The lengths the model gives the GB300 (152 SMs) launches that were swept;
+    each is the measured best or within 1 % of it."""
+    assert lib.spfm_debug_pick_zchunk(tiles, nz, per_sm, 152, 6 * 4 * 152) == want
+
+
+def test_zchunk_model_refuses_bad_arguments(lib):
+    assert lib.spfm_debug_pick_zchunk(0, 10, 4, 152, 100) == -1
+    assert lib.spfm_debug_pick_zchunk(4, 10, 0, 152, 100) == -1
 
 
 def test_last_error_is_thread_local_without_grid(lib):
