@@ -623,7 +623,11 @@ __device__ __forceinline__ P laplace_update(const PCoef &PC, P t, P ph, P h, P g
 // Returns false when a bounded wait gave up (the error word is set).
 // SR: stochastic rounding of the update (FP32 compute only), random bits from
 // sr_hash(padded cell index xor sr_key).
-template <class S, class T, int STENCIL, int KIND, int TX, int TY, int RPT_, bool IMG = false, bool SR = false>
+// ROLL (KIND 5): the group loop stays a loop, for coefficients in the kernel's
+// parameters (single grids); from a batch's grid records in global memory the
+// unrolled loop overlaps the pairs' loads.  Same operations, same bits.
+template <class S, class T, int STENCIL, int KIND, int TX, int TY, int RPT_, bool IMG = false, bool SR = false,
+          bool ROLL = false>
 __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T> &PC,
                                           const S *__restrict__ src, S *__restrict__ dst,
                                           int *__restrict__ err, const CUtensorMap *tmap, int bx,
@@ -880,17 +884,21 @@ __device__ __forceinline__ bool step_tile(const StepCoef<T> &C, const PackCoef<T
                         num[q] = t0.nbeta;
                         den[q] = K::fma(t0.nA, u[q], PC.one);
                     }
+                    auto group = [&](const typename PackCoef<T>::Pair tk) {
 #pragma unroll
-                    for (int kk = 1; kk < NTMAX; ++kk) {
-                        if (kk < PC.nterms) {
-                            const typename PackCoef<T>::Pair tk = PC.pair[kk];
-#pragma unroll
-                            for (int q = 0; q < NP; ++q) {
-                                const P d = K::fma(tk.nA, u[q], PC.one);
-                                num[q] = K::fma(num[q], d, K::mul(tk.nbeta, den[q]));
-                                den[q] = K::mul(den[q], d);
-                            }
+                        for (int q = 0; q < NP; ++q) {
+                            const P d = K::fma(tk.nA, u[q], PC.one);
+                            num[q] = K::fma(num[q], d, K::mul(tk.nbeta, den[q]));
+                            den[q] = K::mul(den[q], d);
                         }
+                    };
+                    if constexpr (ROLL) {
+#pragma unroll 1
+                        for (int kk = 1; kk < PC.nterms; ++kk) group(PC.pair[kk]);
+                    } else {
+#pragma unroll
+                        for (int kk = 1; kk < NTMAX; ++kk)
+                            if (kk < PC.nterms) group(PC.pair[kk]);
                     }
 #pragma unroll
                     for (int q = 0; q < NP; ++q) {
@@ -1033,7 +1041,7 @@ __global__ void __launch_bounds__(TileShape<S, T, TX, TY, RPT_>::NTHREADS,
 #pragma unroll
         for (int f = 0; f < 6; ++f) fwd = fwd && C.g.bc[f] != SPFM_PERIODIC;
     }
-    step_tile<S, T, STENCIL, KIND, TX, TY, RPT_, IMG, SR>(C, PC, src, dst, err, use_tmap ? &tmap : nullptr,
+    step_tile<S, T, STENCIL, KIND, TX, TY, RPT_, IMG, SR, true>(C, PC, src, dst, err, use_tmap ? &tmap : nullptr,
                                                      blockIdx.x, blockIdx.y, zc0, zc1, stages, full, empty, 0,
                                                      true, mode, C.sr_key, ready, fwd);
 }
